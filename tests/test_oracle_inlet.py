@@ -1,0 +1,122 @@
+"""Pins of the oracle's random inlet (Sec. 2.3, Eq. karhunenExp) and its RNG.
+
+Each pin checks the oracle against something other than itself: published
+Philox known-answer vectors, closed forms the paper states in words (axis std
+~0.30, Mach extremes +7.5 % / -8.1 %, +-3 % Mach at one sigma) and the +-1 sigma
+envelope the paper prints in Fig. 1.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt")) if not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+def test_uniforms_are_u_minus1_1():
+    # 20 000 realizations x 20 coefficients: open interval, mean 0, variance 1/3.
+    vals = []
+    for m in range(2000):
+        Y, Z = O.kl_coefficients(0, m)
+        vals.append(Y)
+        vals.append(Z)
+    v = np.concatenate(vals)
+    assert v.min() > -1.0 and v.max() < 1.0
+    assert abs(v.mean()) < 4 * np.sqrt(1 / 3 / v.size)
+    assert abs(v.var() - 1 / 3) < 4 * np.sqrt(4 / 45 / v.size)
+    # coefficients of one realization are independent of the others (prefix property)
+    Y0, Z0 = O.kl_coefficients(0, 7)
+    Y1, Z1 = O.kl_coefficients(0, 7)
+    assert np.array_equal(Y0, Y1) and np.array_equal(Z0, Z1)
+    Y2, _ = O.kl_coefficients(1, 7)
+    assert not np.array_equal(Y0, Y2)
+
+
+def _sigma_closed_form(ybar, jet=O.Jet()):
+    """Std of the KL density at ybar from the oracle's density map, which is affine
+    in (Y, Z): sigma^2 = sum_k Var(Y_k) (d rho/d Y_k)^2 + same for Z, Var = 1/3."""
+    K = jet.K
+    zero = np.zeros(K)
+    base = O.kl_density(ybar, zero, zero, jet)
+    var = 0.0
+    for k in range(K):
+        e = np.zeros(K)
+        e[k] = 1.0
+        var += (O.kl_density(ybar, e, zero, jet) - base) ** 2 / 3.0
+        var += (O.kl_density(ybar, zero, e, jet) - base) ** 2 / 3.0
+    return np.sqrt(var), base
+
+
+def test_axis_std_matches_paper_closed_form():
+    # Sec. 4.3: on the axis the perturbation has std A rho_bar (sum_k k^-4 / 3)^(1/2) ~ 0.30.
+    s, base = _sigma_closed_form(0.0)
+    assert base == 5.0
+    assert abs(s - 0.30032) < 5e-5
+    assert round(s, 2) == 0.30
+    # and the sampled ensemble agrees within its sampling error
+    vals = []
+    for m in range(4000):
+        Y, Z = O.kl_coefficients(0, m)
+        vals.append(O.kl_density(0.0, Y, Z))
+    sd = np.std(vals)
+    assert abs(sd - s) < 4 * s / np.sqrt(2 * len(vals))
+
+
+def test_axis_mach_extremes_and_one_sigma():
+    # Sec. 2.3: Mach ~ sqrt(rho); +-3 % at one sigma, +7.5 % / -8.1 % with all
+    # coefficients at their bounds.
+    K = 10
+    hi = O.kl_density(0.0, np.ones(K), np.zeros(K))
+    lo = O.kl_density(0.0, -np.ones(K), np.zeros(K))
+    assert round(np.sqrt(hi / 5.0) - 1.0, 3) == 0.075
+    assert round(np.sqrt(lo / 5.0) - 1.0, 3) == -0.081
+    s, _ = _sigma_closed_form(0.0)
+    assert round(np.sqrt(1 + s / 5.0) - 1.0, 2) == 0.03
+    # sin terms vanish on the axis: Z does not move the axis density
+    assert O.kl_density(0.0, np.zeros(K), np.ones(K)) == 5.0
+
+
+def test_fig1_envelope_pins_window_and_normalisation():
+    pts = np.loadtxt(os.path.join(GOLD, "fig1_envelope.txt"))
+    yb, up, lo = pts[:, 0], pts[:, 1], pts[:, 2]
+    half = 0.5 * (up - lo)
+    model = np.array([_sigma_closed_form(y)[0] for y in yb])
+    resid = np.abs(model - half)
+    # M = 1000 sampling error of sigma is ~ sigma / sqrt(2M) <= 0.0067; printed to 3 decimals
+    assert resid.max() < 0.012, resid.max()
+    # alternative windows misfit by far more (the pin discriminates W)
+    s0 = _sigma_closed_form(0.0)[0]
+    for alt in (np.ones_like(yb), np.cos(0.5 * np.pi * yb), 1 - yb ** 2):
+        assert np.abs(s0 * alt - half).max() > 0.03
+    # the envelope vanishes at the jet edge (window reaches zero at |ybar| = 1)
+    assert half[0] == 0.0 and half[-1] == 0.0
+
+
+def test_inlet_profile_step_and_energy():
+    g = O.Grid(200, 100)
+    P = O.Params()
+    J = O.Jet()
+    inl = O.inlet(g, P, J, seed=0, m=3)
+    y = g.y0 + (np.arange(g.ny) + 0.5) * g.dx
+    jet = np.abs(y) <= J.r_jet
+    assert jet.sum() == 8  # 0.1 wide jet on dx = 0.0125
+    rho, m1, m2, E = inl
+    assert np.all(rho[~jet] == 0.5) and np.all(m1[~jet] == 0.0)
+    assert np.allclose(m1[jet] / rho[jet], 800.0, rtol=1e-15)
+    assert np.all(m2 == 0.0)
+    # E from the EOS with p = p_amb (Sec. 2.2)
+    p = (P.gamma - 1) * (E - 0.5 * m1 ** 2 / rho)
+    assert np.allclose(p, 0.4127, rtol=1e-8)
+    assert np.all(np.abs(rho[jet] - 5.0) < 5.0 * 0.1 * np.sum(1.0 / np.arange(1, 11) ** 2) + 1e-12)
