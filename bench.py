@@ -1,0 +1,337 @@
+"""Benchmark of the probabilistic VLBM hot path on GB300.
+
+One bench step is one pass of the whole path over one batch: seeded ensemble
+initialisation (Philox + KL inlet, initial condition), S VLBM steps of every
+realization on both grid levels (kinetic speed, primitive recovery,
+Maxwellians, first-order state, faces and limiter, fused update + stream,
+boundaries), density extraction of both levels and the per-cell statistics
+between the levels (restriction, mean, std, one-point W1 from a per-cell sort).
+
+Workload (default): the batched ensemble of M = 1000 jet realizations per GPU
+on the 400 x 200 and 800 x 400 levels in one launch per step, mixed precision.
+Metric: ensemble cell-updates per second (GLUPS) = sum over levels and
+realizations of nx ny x S / wall seconds of the bench step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+LEVELS = [(400, 200), (800, 400)]
+M_PER_GPU = 1000
+SEED = 0
+METRIC = "ensemble cell-updates/s (GLUPS) & % HBM roofline, mixed vs FP64, at stated stat error"
+BYTES_PER_UPDATE = {"mixed": 160, "fp64": 320}
+# DRAM traffic of one step-kernel launch from an ncu capture, with the sha256
+# of the kernel source it was taken on (null once the kernel changes).
+NCU_TRAFFIC = {}
+
+
+def peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sha(precision: str) -> str:
+    name = "vlbm_step_mixed.cu" if precision == "mixed" else "vlbm_step_f64.cu"
+    with open(os.path.join(HERE, "paper_2605_25282_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for s in self.samples for n, v in zip(names, s[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup(gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != gpus:
+        world = max(world, 1)
+    return rank, world, local
+
+
+def cpu_oracle_rate(levels, steps: int, m: int = 0):
+    """The oracle (plain FP64 C, one thread) on one realization of every level."""
+    from oracle import oracle as O
+
+    cells = 0
+    t0 = time.perf_counter()
+    dens = []
+    for (nx, ny) in levels:
+        r = O.run_jet(O.Grid(nx, ny), O.Params(), O.Jet(), SEED, m, 1, steps, want_pops=False)
+        dens.append(r["u"][:, 0])
+        cells += nx * ny * steps
+    O.stats_w1_mean_std(dens[0], dens[1])
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, dt, cells
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    levels = LEVELS
+    per = 6  # solver steps per bounded sample
+    for w in range(args.warmup):
+        cpu_oracle_rate(levels, per, m=w)
+    times = []
+    cells = 0
+    for k in range(args.steps):
+        _, dt, c = cpu_oracle_rate(levels, per, m=args.warmup + k)
+        times.append(dt)
+        cells += c
+    total = sum(times)
+    value = cells / total / 1e9
+    sample = (f"1 realization x ({' + '.join(f'{nx}x{ny}' for nx, ny in levels)}) x {per} VLBM steps per bench "
+              "step, plus the statistics of that sample; FP64 oracle, one thread")
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox jet ensemble)",
+        "impl": "reference",
+        "config": {"workload": "Mach 2000 jet ensemble, 400x200 + 800x400 levels (bounded sample)",
+                   "levels": levels, "solver_steps_per_step": per},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2605_25282_gb300 import vlbm
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    dev = torch.device("cuda", local)
+    # every launch of the bench runs on one non-default stream: the library's
+    # kernels, the statistics, the copies and the CUDA events
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    levels = LEVELS
+    M = args.m
+    S = args.solver_steps
+    prec = args.precision
+    ens = vlbm.Ensemble(levels, precision=prec, stream=stream)
+    m_begin = rank * M
+    cells_per_solver_step = sum(nx * ny for nx, ny in levels) * M
+    (nxa, nya), (nxb, nyb) = levels
+    dens_a = torch.empty((M, nya, nxa), dtype=torch.float32, device=dev)
+    dens_b = torch.empty((M, nyb, nxb), dtype=torch.float32, device=dev)
+    host_out = [torch.empty((nya, nxa), dtype=torch.float64, pin_memory=True) for _ in range(5)]
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    step_ms = []
+
+    def bench_step(e2e: bool, timed: bool):
+        ens.init(SEED, M, m_begin=m_begin)
+        if timed:
+            ev[0].record(stream)
+        ens.step(S)
+        if timed:
+            ev[1].record(stream)
+        ens.density(0, out=dens_a)
+        ens.density(1, out=dens_b)
+        st = vlbm.stats_w1_mean_std(dens_a, dens_b, stream=stream)
+        if e2e:
+            for h, k in zip(host_out, ("mean_a", "std_a", "mean_b", "std_b", "w1")):
+                h.copy_(st[k], non_blocking=True)
+        return st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed_loop(e2e: bool):
+        for _ in range(args.warmup):
+            bench_step(e2e, False)
+        barrier()
+        launches0 = vlbm.kernel_launches()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            bench_step(e2e, not e2e)
+            if not e2e:
+                torch.cuda.synchronize()
+                step_ms.append(ev[0].elapsed_time(ev[1]))
+        t1.record(stream)
+        barrier()
+        ms = t0.elapsed_time(t1)
+        launches = vlbm.kernel_launches() - launches0
+        if dist is not None:
+            tt = torch.tensor([ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, launches
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = timed_loop(False)
+    clk = clocks.stop()
+    ms_e2e, _ = timed_loop(True)
+
+    # the FP64 path on the same levels, fewer realizations (rate per cell update)
+    fp64 = None
+    if args.fp64_m > 0 and prec == "mixed":
+        e64 = vlbm.Ensemble(levels, precision="fp64", stream=stream)
+        e64.init(SEED, args.fp64_m, m_begin=m_begin)
+        e64.step(2)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e64.step(args.fp64_steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        c64 = sum(nx * ny for nx, ny in levels) * args.fp64_m * args.fp64_steps
+        r64 = c64 / t64 / 1e9
+        hbm, src = peaks()
+        fp64 = {"value": r64, "unit": "GLUPS", "M": args.fp64_m, "solver_steps": args.fp64_steps,
+                "hbm_frac": r64 * 1e9 * BYTES_PER_UPDATE["fp64"] / (hbm * 1e9)}
+        e64.close()
+
+    total_cells = cells_per_solver_step * S * args.steps * world
+    value = total_cells / (ms / 1e3) / 1e9
+    e2e_value = total_cells / (ms_e2e / 1e3) / 1e9
+    hbm, src = peaks()
+    kern_s = float(np.mean(step_ms)) / 1e3 / S
+    achieved = BYTES_PER_UPDATE[prec] * cells_per_solver_step / kern_s / 1e9
+    sha = kernel_sha(prec)
+    tr = NCU_TRAFFIC.get(prec)
+    traffic = tr["bytes_per_launch"] if tr and tr["sha"] == sha else None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, dt, c = cpu_oracle_rate(levels, args.cpu_steps)
+        cpu = {"value": r, "unit": "GLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"1 realization x (400x200 + 800x400) x {args.cpu_steps} VLBM steps + statistics, "
+                         f"{dt:.1f} s of one host core"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
+            "data": "synthetic (seeded Philox4x32-10 Karhunen-Loeve jet inlets)",
+            "config": {"workload": f"Mach 2000 jet ensemble, M={M} per GPU, levels 400x200 + 800x400 "
+                                   f"in one launch, {prec}, R-theta limiter, {S} VLBM steps + init + "
+                                   f"density + W1/mean/std statistics per bench step",
+                       "levels": levels, "M_per_gpu": M, "solver_steps_per_step": S, "precision": prec,
+                       "l2": "inputs larger than L2 (lattice state "
+                             f"{2 * cells_per_solver_step * BYTES_PER_UPDATE[prec] / 2 / 1e9:.0f} GB)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "kernel": f"step_{prec}_kernel", "peak_source": f"{src} hbm_gbs",
+                         "bytes_per_cell_update": BYTES_PER_UPDATE[prec],
+                         "note": "kernel time = CUDA-event time of the S-step graph / S (includes the "
+                                 "per-step tick kernel)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 5 * nxa * nya * 8,
+                    "note": "public API with the statistics read back to pinned host memory every step; the "
+                            "ensemble inputs are defined by the seed and drawn on the device"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "fp64_path": fp64,
+            "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+        }
+        print(json.dumps(line), flush=True)
+    ens.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--m", type=int, default=M_PER_GPU)
+    ap.add_argument("--solver-steps", type=int, default=64)
+    ap.add_argument("--fp64-m", type=int, default=50)
+    ap.add_argument("--fp64-steps", type=int, default=8)
+    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * libvlbm: GB300 (sm_103a) implementation of the probabilistic vectorial lattice
+ * Boltzmann method (VLBM) for Monte-Carlo ensembles of the Mach 2000 jet, from
+ * "Computing statistical solutions of a Mach 2000 astrophysical jet".
+ *
+ * Conventions shared by every call:
+ *   - Plain C ABI: plain pointers and sizes, no exceptions cross the boundary;
+ *     every call returns a vlbm_status (VLBM_OK = 0) and, on failure, records a
+ *     message readable with vlbm_last_error().
+ *   - Work is enqueued on the CUDA stream given to vlbm_create and is
+ *     asynchronous unless a call says otherwise.  Calls that read results back
+ *     to the host (vlbm_time, vlbm_sync, vlbm_save) synchronise that stream.
+ *   - "device pointer" arguments must be CUDA device (or managed) memory owned
+ *     by the caller; the library never frees them.
+ *   - Field layouts are realization-major and row-major with x fastest:
+ *     field[r][j][i] for r = 0..count-1, j = 0..ny-1, i = 0..nx-1.
+ *   - Node placement: x_i = i dx (the inlet column sits at x = 0),
+ *     y_j = y_min + (j + 1/2) dx, dx = x_max / nx; cells are square.
+ */
+#ifndef VLBM_H
+#define VLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vlbm_ctx vlbm_ctx;
+
+/* Status codes. */
+typedef enum {
+  VLBM_OK = 0,
+  VLBM_EINVAL = 1,        /* invalid argument (message says which) */
+  VLBM_ENOMEM = 2,        /* device allocation failed */
+  VLBM_ECUDA = 3,         /* a CUDA runtime call failed */
+  VLBM_ENONPOSITIVE = 4,  /* a realization produced rho <= 0 or p <= 0 (sticky) */
+  VLBM_ENONFINITE = 5,    /* a realization produced a non-finite value (sticky) */
+  VLBM_ETIMEOUT = 6,      /* a bounded device wait gave up */
+  VLBM_ESTATE = 7         /* call out of order (e.g. step before init_ensemble) */
+} vlbm_status;
+
+/* Arithmetic of the solver (fixed at creation). */
+enum {
+  /* Conserved variables and raw populations in FP64, the paper's arithmetic
+   * in the lab frame (320 B per cell update). */
+  VLBM_FP64 = 0,
+  /* FP32 storage of the nodal state (rho, v1, v2, p) and of the populations'
+   * non-equilibrium parts, expressed in each node's rest frame; the update is
+   * evaluated in the frame moving with the node so that pressure never comes
+   * from E - |m|^2 / (2 rho) (160 B per cell update). */
+  VLBM_MIXED = 1
+};
+
+/* Blending-parameter rule (Sec. 2.1: theta in [0, 1] per face). */
+enum {
+  VLBM_LIMITER_NONE = 0,       /* theta = 0: first-order scheme */
+  VLBM_LIMITER_UNLIMITED = 1,  /* theta = 1: unlimited second-order scheme (tests) */
+  VLBM_LIMITER_RTHETA = 2      /* convex-split positivity + relaxed local bounds */
+};
+
+/* One grid level on [0, x_max] x [y_min, y_max]; requires
+ * x_max / nx == (y_max - y_min) / ny (square cells), nx, ny >= 3. */
+typedef struct {
+  int nx, ny;
+  double x_max, y_min, y_max;
+} vlbm_grid;
+
+/* Primitive state (rho, velocity (u, v), pressure).  Sec. 2.2: the jet is
+ * {5, 800, 0, 0.4127}, the ambient medium {0.5, 0, 0, 0.4127}. */
+typedef struct {
+  double rho, u, v, p;
+} vlbm_prim;
+
+/* Relaxation / limiting parameters.
+ *   alpha    weight of the rest population M_5 = alpha u (Eq. maxwellians5), [0, 1)
+ *   kappa    safety factor on the kinetic speed, a_n = kappa 2 lambda / (1 - alpha), >= 1
+ *   limiter  VLBM_LIMITER_*
+ *   rlmp_rel, rlmp_abs  widening of the local density bounds:
+ *            [lo - d, hi + d], d = rlmp_rel (hi - lo) + rlmp_abs
+ *   eps_pos  positivity floor for rho and p (the floor is min(eps_pos, value of
+ *            the first-order state)) */
+typedef struct {
+  double alpha, kappa;
+  int limiter;
+  double rlmp_rel, rlmp_abs, eps_pos;
+} vlbm_relax;
+
+/* Inlet perturbation, Eq. (karhunenExp):
+ *   rho' = rho_jet [1 + sum_{k<=K} amp_k (Y_k cos(k pi yb) + Z_k sin(k pi yb)) W(yb)],
+ *   yb = y / r_jet, W = cos^2(pi yb / 2), amp_k = A k^-p_decay, or amp[k-1]
+ *   when use_amp != 0.  Y_k, Z_k ~ U(-1, 1) from Philox4x32-10 with
+ *   key = seed and counter = (m, block, 0, 0) (K <= 16).  r_jet is also the
+ *   half-width of the inlet velocity step (Sec. 2.2). */
+typedef struct {
+  double r_jet, A, p_decay;
+  int K;
+  double amp[16];
+  int use_amp;
+} vlbm_perturb;
+
+/* Device memory callbacks (e.g. a framework's caching allocator).  alloc
+ * returns a 256-byte aligned device pointer or NULL. */
+typedef void* (*vlbm_alloc_fn)(size_t bytes, void* user);
+typedef void (*vlbm_free_fn)(void* ptr, void* user);
+
+/* Paper defaults: alpha 0, kappa 1, R-theta limiter with rlmp_rel 0.1,
+ * rlmp_abs 0, eps_pos 1e-13; r_jet 0.05, A 0.1, p_decay 2, K 10. */
+void vlbm_default_relax(vlbm_relax* relax);
+void vlbm_default_perturb(vlbm_perturb* perturb);
+
+/* Sec. 2.1-2.2: validates the problem (grids, gamma > 1, states with
+ * rho, p > 0) and creates a context.  Several levels (e.g. the refinement
+ * ladder of Sec. 3.3) advance together in every call.  cuda_stream may be
+ * NULL: the context then creates and owns a non-blocking stream.  alloc/free
+ * may be NULL (cudaMalloc/cudaFree).
+ * No device work is done here.  On success *out owns the context. */
+int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_prim* jet,
+                const vlbm_prim* ambient, const vlbm_relax* relax, int precision, void* cuda_stream,
+                vlbm_alloc_fn alloc, vlbm_free_fn free_fn, void* alloc_user, vlbm_ctx** out);
+
+/* Sec. 2.3, Eqs. (karhunenExp), (rho_inlet_def), (u0_def): allocates the state
+ * of M realizations on every level (re-allocates if M changes), draws the inlet
+ * density of realization m = 0..M-1, sets the initial condition with
+ * equilibrium populations and resets t = 0, steps = 0.  perturb may be NULL
+ * (defaults).  Realization m is identical for every M > m (nested prefixes). */
+int vlbm_init_ensemble(vlbm_ctx* ctx, uint64_t seed, int M, const vlbm_perturb* perturb);
+
+/* As vlbm_init_ensemble, for the block of realizations m_begin..m_begin+M-1
+ * of the same nested sequence (Sec. 3.1: realization m is fixed by the seed and
+ * m alone), so that independent processes can each own a block of one ensemble.
+ * Local index r of the context holds global realization m_begin + r. */
+int vlbm_init_ensemble_block(vlbm_ctx* ctx, uint64_t seed, int m_begin, int M, const vlbm_perturb* perturb);
+
+/* Sec. 2.1, Eqs. (vlbm1)-(vlbm5), with a_n re-evaluated every step
+ * (Sec. 2.3): advances every realization on every level by n steps. */
+int vlbm_step(vlbm_ctx* ctx, int n);
+
+/* Advances every realization until its own time reaches t exactly; the last
+ * step of each lands on t (a_n <- max(a_n, dx / (t - t_n))).  Realizations
+ * that finish early stop stepping.  Synchronises the stream. */
+int vlbm_advance_to(vlbm_ctx* ctx, double t);
+
+/* Eq. (eos): writes rho, velocity (u, v) and p of realizations m0..m0+count-1
+ * of one level into caller device buffers laid out [count][ny][nx] (FP64).
+ * Any output pointer may be NULL. */
+int vlbm_moments(vlbm_ctx* ctx, int level, int m0, int count, double* rho, double* u, double* v,
+                 double* p);
+
+/* Density only, [count][ny][nx], FP32 (as_f32 != 0) or FP64; the input layout
+ * of stats_w1_mean_std. */
+int vlbm_density(vlbm_ctx* ctx, int level, int m0, int count, void* rho, int as_f32);
+
+/* Host copies of the per-realization time and step count of one level
+ * (arrays of length M; either may be NULL).  Synchronises the stream and
+ * returns the first sticky error flag of the level, if any. */
+int vlbm_time(vlbm_ctx* ctx, int level, double* t_host, long long* steps_host);
+
+/* Waits for the stream and reports sticky per-realization flags:
+ * VLBM_ENONPOSITIVE / VLBM_ENONFINITE if any realization raised one. */
+int vlbm_sync(vlbm_ctx* ctx);
+
+/* Full state of realizations m0..m0+count-1 as FP64 device arrays:
+ * u [count][4][ny][nx] conserved (rho, rho v1, rho v2, E) and pops
+ * [count][16][ny][nx] (population k = 1..4 at rows 4(k-1)..4(k-1)+3).
+ * In VLBM_MIXED the populations are rebuilt from the stored non-equilibrium
+ * parts.  pops may be NULL. */
+int vlbm_get_state(vlbm_ctx* ctx, int level, int m0, int count, double* u, double* pops);
+
+/* Overwrites the state of realizations m0..m0+count-1 (same layouts as
+ * vlbm_get_state, device pointers), resets their t and step count to 0 and
+ * re-evaluates their kinetic speed.  The inlet column keeps its Dirichlet
+ * datum from vlbm_init_ensemble at the next step. */
+int vlbm_set_state(vlbm_ctx* ctx, int level, int m0, int count, const double* u, const double* pops);
+
+/* Sec. 3.2 and 3.4, Eqs. (mean), (std), (w1disc): per-cell statistics between
+ * ensemble a [M][nya][nxa] and ensemble b [M][nyb][nxb] (device pointers; FP32
+ * when *_is_f32 != 0, else FP64).  When nxb = r nxa and nyb = r nya (r >= 1)
+ * each realization of b is first block-averaged onto a's grid.  Outputs
+ * (device, FP64, [nya][nxa], any may be NULL): mean and population std of a and
+ * of the restricted b, and the one-point W1 = (1/M) sum_m |a_(m) - b_(m)| over
+ * the ascending order statistics.  1 <= M <= 4096.  Asynchronous on
+ * cuda_stream (may be NULL). */
+int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b,
+                      int b_is_f32, int nxb, int nyb, int M, double* mean_a, double* std_a,
+                      double* mean_b, double* std_b, double* w1, void* cuda_stream);
+
+/* Checkpoint of the whole context state (every level and realization, times,
+ * step counts, kinetic-speed bookkeeping) to host memory.  With host_buf NULL,
+ * *bytes receives the size needed.  Synchronises the stream.  Restoring with
+ * vlbm_load into a context created with the same levels, precision and M
+ * resumes bit-identically. */
+int vlbm_save(vlbm_ctx* ctx, void* host_buf, size_t* bytes);
+int vlbm_load(vlbm_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Message of the last failing call on ctx (or of the last failing call in this
+ * thread when ctx is NULL).  Never NULL. */
+const char* vlbm_last_error(const vlbm_ctx* ctx);
+
+/* Number of kernel launches this library has enqueued in this process so far
+ * (graph replays count every kernel node).  Instrumentation for benchmarks. */
+unsigned long long vlbm_kernel_launches(void);
+
+/* Frees the context and everything it allocated.  Accepts NULL. */
+void vlbm_destroy(vlbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLBM_H */

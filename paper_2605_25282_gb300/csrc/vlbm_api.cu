@@ -1,0 +1,577 @@
+// Host side of the C ABI declared in include/vlbm.h: validation, device
+// memory, the per-step launch sequence and its CUDA-graph capture, I/O.
+//
+// One step of the ensemble is two launches on the context stream:
+//   step kernel  (every level, realization and tile in one grid)
+//   tick kernel  (per realization: t, step count, lambda -> a_{n+1}, landing)
+// vlbm_step / vlbm_advance_to replay a captured graph of kGraphSteps such
+// pairs, so a long run costs one graph launch per kGraphSteps steps.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vlbm_internal.cuh"
+
+namespace vlbm {
+int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32, int nxb,
+                 int nyb, int M, double* mean_a, double* std_a, double* mean_b, double* std_b, double* w1,
+                 cudaStream_t s, const char** why);
+void tiles_f64(int nx, int ny, int* tx, int* ty);
+void tiles_mixed(int nx, int ny, int* tx, int* ty);
+}  // namespace vlbm
+
+using namespace vlbm;
+
+namespace {
+
+constexpr int kGraphSteps = 32;
+constexpr uint32_t kSaveMagic = 0x564c424du;  // "VLBM"
+constexpr uint32_t kSaveVersion = 1;
+
+thread_local std::string g_thread_error = "no error";
+std::atomic<unsigned long long> g_launches{0};
+thread_local bool g_capturing = false;
+
+struct LevelMem {
+  void* lat = nullptr;
+  double* inlet = nullptr;
+  RealState* rs = nullptr;
+  size_t lat_bytes = 0, inlet_bytes = 0, rs_bytes = 0;
+};
+
+}  // namespace
+
+namespace vlbm {
+void add_launches(unsigned n) {
+  if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+}  // namespace vlbm
+
+struct vlbm_ctx {
+  std::vector<vlbm_grid> grids;
+  Physics ph{};
+  int precision = VLBM_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  vlbm_alloc_fn alloc = nullptr;
+  vlbm_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  int M = 0;
+  bool initialized = false;
+  bool prepared = false;
+  double target = std::numeric_limits<double>::infinity();
+  std::vector<LevelMem> mem;
+  Launch launch{};
+  int* d_count = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool warmed = false;
+  std::string err = "no error";
+};
+
+namespace {
+
+int fail(vlbm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  g_thread_error = msg;
+  return code;
+}
+
+int cuda_fail(vlbm_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, VLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(vlbm_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (c->alloc) return c->alloc(bytes, c->user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(vlbm_ctx* c, void* p) {
+  if (!p) return;
+  if (c->free_fn)
+    c->free_fn(p, c->user);
+  else if (!c->alloc)
+    cudaFree(p);
+}
+
+void release_levels(vlbm_ctx* c) {
+  for (auto& m : c->mem) {
+    dev_free(c, m.lat);
+    dev_free(c, m.inlet);
+    dev_free(c, m.rs);
+  }
+  c->mem.clear();
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->warmed = false;
+}
+
+int launch_one_step(vlbm_ctx* c) {
+  cudaError_t e = c->precision == VLBM_FP64 ? launch_step_f64(c->launch, c->stream)
+                                             : launch_step_mixed(c->launch, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+  e = launch_tick(c->launch, c->precision, 1, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "tick kernel launch");
+  return VLBM_OK;
+}
+
+int build_graph(vlbm_ctx* c) {
+  if (c->graph) return VLBM_OK;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+  int st = VLBM_OK;
+  g_capturing = true;
+  for (int s = 0; s < kGraphSteps && st == VLBM_OK; ++s) st = launch_one_step(c);
+  g_capturing = false;
+  e = cudaStreamEndCapture(c->stream, &g);
+  if (st != VLBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  return VLBM_OK;
+}
+
+int run_steps(vlbm_ctx* c, long long n) {
+  // the first steps run as plain launches (this also configures the kernels'
+  // shared-memory limits before any capture)
+  while (n > 0 && !c->warmed) {
+    int st = launch_one_step(c);
+    if (st) return st;
+    --n;
+    c->warmed = true;
+  }
+  while (n >= kGraphSteps) {
+    int st = build_graph(c);
+    if (st) return st;
+    cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    add_launches(2 * kGraphSteps);
+    n -= kGraphSteps;
+  }
+  while (n-- > 0) {
+    int st = launch_one_step(c);
+    if (st) return st;
+  }
+  return VLBM_OK;
+}
+
+int prepare(vlbm_ctx* c, double target) {
+  if (c->prepared && (c->target == target || (std::isinf(c->target) && std::isinf(target)))) return VLBM_OK;
+  cudaError_t e = launch_set_target(c->launch, target, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_target");
+  e = launch_tick(c->launch, c->precision, 0, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "tick");
+  c->target = target;
+  c->prepared = true;
+  return VLBM_OK;
+}
+
+int read_flags(vlbm_ctx* c, int level_only, std::vector<RealState>* out_level) {
+  int worst = VLBM_OK;
+  for (int l = 0; l < (int)c->mem.size(); ++l) {
+    if (level_only >= 0 && l != level_only) continue;
+    std::vector<RealState> h(c->M);
+    cudaError_t e = cudaMemcpy(h.data(), c->mem[l].rs, sizeof(RealState) * c->M, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading realization state");
+    for (int m = 0; m < c->M; ++m) {
+      if (h[m].flags & 2) {
+        worst = VLBM_ENONFINITE;
+        fail(c, worst, "level " + std::to_string(l) + " realization " + std::to_string(m) + ": non-finite state");
+      } else if ((h[m].flags & 1) && worst == VLBM_OK) {
+        worst = VLBM_ENONPOSITIVE;
+        fail(c, worst,
+             "level " + std::to_string(l) + " realization " + std::to_string(m) + ": rho or p not positive");
+      }
+    }
+    if (out_level) *out_level = h;
+  }
+  return worst;
+}
+
+int check_level(vlbm_ctx* c, int level, int m0, int count) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  if (!c->initialized) return fail(c, VLBM_ESTATE, "vlbm_init_ensemble has not been called");
+  if (level < 0 || level >= (int)c->grids.size()) return fail(c, VLBM_EINVAL, "level out of range");
+  if (m0 < 0 || count < 0 || m0 + count > c->M) return fail(c, VLBM_EINVAL, "realization range out of [0, M)");
+  return VLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vlbm_default_relax(vlbm_relax* r) {
+  if (!r) return;
+  r->alpha = 0.0;
+  r->kappa = 1.0;
+  r->limiter = VLBM_LIMITER_RTHETA;
+  r->rlmp_rel = 0.1;
+  r->rlmp_abs = 0.0;
+  r->eps_pos = 1e-13;
+}
+
+void vlbm_default_perturb(vlbm_perturb* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->r_jet = 0.05;
+  p->A = 0.1;
+  p->p_decay = 2.0;
+  p->K = 10;
+  p->use_amp = 0;
+}
+
+int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_prim* jet,
+                const vlbm_prim* ambient, const vlbm_relax* relax, int precision, void* cuda_stream,
+                vlbm_alloc_fn alloc, vlbm_free_fn free_fn, void* alloc_user, vlbm_ctx** out) {
+  if (!out) return fail(nullptr, VLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!levels || nlevels < 1 || nlevels > kMaxLevels)
+    return fail(nullptr, VLBM_EINVAL, "need 1..8 grid levels");
+  if (!jet || !ambient) return fail(nullptr, VLBM_EINVAL, "jet and ambient states are required");
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, VLBM_EINVAL, "gamma must be > 1");
+  if (!(jet->rho > 0) || !(jet->p > 0) || !(ambient->rho > 0) || !(ambient->p > 0))
+    return fail(nullptr, VLBM_EINVAL, "jet and ambient states need rho > 0 and p > 0");
+  if (precision != VLBM_FP64 && precision != VLBM_MIXED) return fail(nullptr, VLBM_EINVAL, "unknown precision");
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, VLBM_EINVAL, "alloc and free callbacks must be given together");
+  vlbm_relax R;
+  vlbm_default_relax(&R);
+  if (relax) R = *relax;
+  if (!(R.alpha >= 0.0 && R.alpha < 1.0)) return fail(nullptr, VLBM_EINVAL, "alpha must be in [0, 1)");
+  if (!(R.kappa >= 1.0)) return fail(nullptr, VLBM_EINVAL, "kappa must be >= 1 (Bouchut bound)");
+  if (R.limiter < 0 || R.limiter > 2) return fail(nullptr, VLBM_EINVAL, "unknown limiter");
+  if (!(R.rlmp_rel >= 0.0) || !(R.rlmp_abs >= 0.0) || !(R.eps_pos >= 0.0))
+    return fail(nullptr, VLBM_EINVAL, "rlmp_rel, rlmp_abs and eps_pos must be >= 0");
+  for (int l = 0; l < nlevels; ++l) {
+    const vlbm_grid& g = levels[l];
+    if (g.nx < 3 || g.ny < 3) return fail(nullptr, VLBM_EINVAL, "every level needs nx, ny >= 3");
+    if ((long long)g.nx * g.ny > (1LL << 31)) return fail(nullptr, VLBM_EINVAL, "level too large");
+    if (!(g.x_max > 0) || !(g.y_max > g.y_min)) return fail(nullptr, VLBM_EINVAL, "empty domain");
+    const double dx = g.x_max / g.nx, dy = (g.y_max - g.y_min) / g.ny;
+    if (std::fabs(dx - dy) > 1e-12 * dx) return fail(nullptr, VLBM_EINVAL, "cells must be square");
+  }
+  vlbm_ctx* c = new (std::nothrow) vlbm_ctx();
+  if (!c) return fail(nullptr, VLBM_ENOMEM, "host allocation failed");
+  c->grids.assign(levels, levels + nlevels);
+  c->ph.gamma = gamma;
+  c->ph.alpha = R.alpha;
+  c->ph.kappa = R.kappa;
+  c->ph.limiter = R.limiter;
+  c->ph.rlmp_rel = R.rlmp_rel;
+  c->ph.rlmp_abs = R.rlmp_abs;
+  c->ph.eps_pos = R.eps_pos;
+  c->ph.jet_rho = jet->rho;
+  c->ph.jet_u = jet->u;
+  c->ph.jet_v = jet->v;
+  c->ph.jet_p = jet->p;
+  c->ph.amb_rho = ambient->rho;
+  c->ph.amb_u = ambient->u;
+  c->ph.amb_v = ambient->v;
+  c->ph.amb_p = ambient->p;
+  c->precision = precision;
+  c->alloc = alloc;
+  c->free_fn = free_fn;
+  c->user = alloc_user;
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(nullptr, e, "cudaStreamCreate");
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return VLBM_OK;
+}
+
+int vlbm_init_ensemble(vlbm_ctx* c, uint64_t seed, int M, const vlbm_perturb* perturb) {
+  return vlbm_init_ensemble_block(c, seed, 0, M, perturb);
+}
+
+int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb* perturb) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  if (M < 1 || M > 65535) return fail(c, VLBM_EINVAL, "M must be in [1, 65535]");
+  if (m_begin < 0 || (long long)m_begin + M > 0xffffffffLL)
+    return fail(c, VLBM_EINVAL, "realization block must lie in [0, 2^32)");
+  vlbm_perturb P;
+  vlbm_default_perturb(&P);
+  if (perturb) P = *perturb;
+  if (P.K < 0 || P.K > kMaxModes) return fail(c, VLBM_EINVAL, "K must be in [0, 16]");
+  if (!(P.r_jet > 0.0)) return fail(c, VLBM_EINVAL, "r_jet must be > 0");
+  if (c->M != M || c->mem.empty()) {
+    release_levels(c);
+    c->mem.resize(c->grids.size());
+    for (size_t l = 0; l < c->grids.size(); ++l) {
+      const vlbm_grid& g = c->grids[l];
+      const int nx_pad = (g.nx + 31) / 32 * 32;
+      const size_t plane = (size_t)g.ny * nx_pad;
+      const size_t real = c->precision == VLBM_FP64 ? 20 * plane * sizeof(double) : 5 * plane * sizeof(float4);
+      LevelMem& mm = c->mem[l];
+      mm.lat_bytes = 2 * (size_t)M * real;
+      mm.inlet_bytes = (size_t)M * 4 * g.ny * sizeof(double);
+      mm.rs_bytes = (size_t)M * sizeof(RealState);
+      mm.lat = dev_alloc(c, mm.lat_bytes);
+      mm.inlet = static_cast<double*>(dev_alloc(c, mm.inlet_bytes));
+      mm.rs = static_cast<RealState*>(dev_alloc(c, mm.rs_bytes));
+      if (!mm.lat || !mm.inlet || !mm.rs) {
+        release_levels(c);
+        c->M = 0;
+        c->initialized = false;
+        return fail(c, VLBM_ENOMEM,
+                    "device allocation of " + std::to_string(mm.lat_bytes) + " bytes for level " +
+                        std::to_string(l) + " failed");
+      }
+    }
+    if (!c->d_count) {
+      c->d_count = static_cast<int*>(dev_alloc(c, sizeof(int)));
+      if (!c->d_count) return fail(c, VLBM_ENOMEM, "device allocation failed");
+    }
+    c->M = M;
+  }
+  // launch descriptor
+  Launch& L = c->launch;
+  L = Launch{};
+  L.ph = c->ph;
+  L.nlevels = (int)c->grids.size();
+  L.M = M;
+  int tiles = 0;
+  for (int l = 0; l < L.nlevels; ++l) {
+    const vlbm_grid& g = c->grids[l];
+    LevelDesc& D = L.lv[l];
+    D.nx = g.nx;
+    D.ny = g.ny;
+    D.nx_pad = (g.nx + 31) / 32 * 32;
+    D.dx = g.x_max / g.nx;
+    D.y_min = g.y_min;
+    D.plane = (size_t)g.ny * D.nx_pad;
+    D.real_stride = c->precision == VLBM_FP64 ? 20 * D.plane : 5 * D.plane;
+    if (c->precision == VLBM_FP64)
+      tiles_f64(g.nx, g.ny, &D.tiles_x, &D.tiles_y);
+    else
+      tiles_mixed(g.nx, g.ny, &D.tiles_x, &D.tiles_y);
+    D.tile_begin = tiles;
+    tiles += D.tiles_x * D.tiles_y;
+    D.lat = c->mem[l].lat;
+    D.inlet = c->mem[l].inlet;
+    D.rs = c->mem[l].rs;
+  }
+  L.total_tiles = tiles;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaError_t e;
+  for (int l = 0; l < L.nlevels; ++l) {
+    e = cudaMemsetAsync(c->mem[l].lat, 0, c->mem[l].lat_bytes, c->stream);
+    add_launches(1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clearing the lattice");
+  }
+  e = launch_inlet(L, seed, m_begin, P, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "inlet kernel");
+  e = launch_init_state(L, c->precision, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "initial state kernel");
+  for (int l = 0; l < L.nlevels; ++l) {
+    e = launch_lambda(L, c->precision, l, 0, M, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "kinetic speed kernel");
+    if (c->precision == VLBM_FP64) {
+      e = launch_fill_equilibrium_f64(L, l, 0, M, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "equilibrium kernel");
+    }
+  }
+  c->initialized = true;
+  c->prepared = false;
+  return VLBM_OK;
+}
+
+int vlbm_step(vlbm_ctx* c, int n) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  if (!c->initialized) return fail(c, VLBM_ESTATE, "vlbm_init_ensemble has not been called");
+  if (n < 0) return fail(c, VLBM_EINVAL, "n must be >= 0");
+  int st = prepare(c, std::numeric_limits<double>::infinity());
+  if (st) return st;
+  return run_steps(c, n);
+}
+
+int vlbm_advance_to(vlbm_ctx* c, double t) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  if (!c->initialized) return fail(c, VLBM_ESTATE, "vlbm_init_ensemble has not been called");
+  if (!(t >= 0.0) || !std::isfinite(t)) return fail(c, VLBM_EINVAL, "t must be finite and >= 0");
+  int st = prepare(c, t);
+  if (st) return st;
+  for (long long guard = 0; guard < (1LL << 40); guard += kGraphSteps) {
+    cudaError_t e = launch_count_active(c->launch, c->d_count, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "count kernel");
+    int h = 0;
+    e = cudaMemcpyAsync(&h, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the active count");
+    if (h == 0) break;
+    st = run_steps(c, kGraphSteps);
+    if (st) return st;
+  }
+  return read_flags(c, -1, nullptr);
+}
+
+int vlbm_moments(vlbm_ctx* c, int level, int m0, int count, double* rho, double* u, double* v, double* p) {
+  int st = check_level(c, level, m0, count);
+  if (st) return st;
+  if (count == 0) return VLBM_OK;
+  cudaError_t e = launch_moments(c->launch, c->precision, level, m0, count, rho, u, v, p, c->stream);
+  return e == cudaSuccess ? VLBM_OK : cuda_fail(c, e, "moments kernel");
+}
+
+int vlbm_density(vlbm_ctx* c, int level, int m0, int count, void* rho, int as_f32) {
+  int st = check_level(c, level, m0, count);
+  if (st) return st;
+  if (!rho) return fail(c, VLBM_EINVAL, "rho is NULL");
+  if (count == 0) return VLBM_OK;
+  cudaError_t e = launch_density(c->launch, c->precision, level, m0, count, rho, as_f32, c->stream);
+  return e == cudaSuccess ? VLBM_OK : cuda_fail(c, e, "density kernel");
+}
+
+int vlbm_time(vlbm_ctx* c, int level, double* t_host, long long* steps_host) {
+  int st = check_level(c, level, 0, 0);
+  if (st) return st;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  std::vector<RealState> h;
+  st = read_flags(c, level, &h);
+  for (int m = 0; m < c->M; ++m) {
+    if (t_host) t_host[m] = h[m].t;
+    if (steps_host) steps_host[m] = h[m].steps;
+  }
+  return st;
+}
+
+int vlbm_sync(vlbm_ctx* c) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  if (!c->initialized) return VLBM_OK;
+  return read_flags(c, -1, nullptr);
+}
+
+int vlbm_get_state(vlbm_ctx* c, int level, int m0, int count, double* u, double* pops) {
+  int st = check_level(c, level, m0, count);
+  if (st) return st;
+  if (!u) return fail(c, VLBM_EINVAL, "u is NULL");
+  if (count == 0) return VLBM_OK;
+  cudaError_t e = launch_get_state(c->launch, c->precision, level, m0, count, u, pops, c->stream);
+  return e == cudaSuccess ? VLBM_OK : cuda_fail(c, e, "get_state kernel");
+}
+
+int vlbm_set_state(vlbm_ctx* c, int level, int m0, int count, const double* u, const double* pops) {
+  int st = check_level(c, level, m0, count);
+  if (st) return st;
+  if (!u || !pops) return fail(c, VLBM_EINVAL, "u and pops are required");
+  if (count == 0) return VLBM_OK;
+  cudaError_t e = launch_set_state(c->launch, c->precision, level, m0, count, u, pops, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_state kernels");
+  c->prepared = false;
+  return VLBM_OK;
+}
+
+int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32,
+                      int nxb, int nyb, int M, double* mean_a, double* std_a, double* mean_b, double* std_b,
+                      double* w1, void* cuda_stream) {
+  const char* why = "";
+  int st = stats_launch(ens_a, a_is_f32, nxa, nya, ens_b, b_is_f32, nxb, nyb, M, mean_a, std_a, mean_b, std_b, w1,
+                        static_cast<cudaStream_t>(cuda_stream), &why);
+  if (st) return fail(nullptr, st, why);
+  return VLBM_OK;
+}
+
+int vlbm_save(vlbm_ctx* c, void* host_buf, size_t* bytes) {
+  if (!c || !bytes) return fail(c, VLBM_EINVAL, "ctx and bytes are required");
+  if (!c->initialized) return fail(c, VLBM_ESTATE, "nothing to save before vlbm_init_ensemble");
+  size_t need = 5 * sizeof(uint32_t) + sizeof(uint8_t) * 8;
+  for (auto& m : c->mem) need += m.rs_bytes + m.inlet_bytes + m.lat_bytes;
+  if (!host_buf) {
+    *bytes = need;
+    return VLBM_OK;
+  }
+  if (*bytes < need) return fail(c, VLBM_EINVAL, "host buffer too small");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  unsigned char* p = static_cast<unsigned char*>(host_buf);
+  const uint32_t hdr[5] = {kSaveMagic, kSaveVersion, (uint32_t)c->precision, (uint32_t)c->grids.size(),
+                           (uint32_t)c->M};
+  std::memcpy(p, hdr, sizeof(hdr));
+  p += sizeof(hdr);
+  std::memset(p, 0, 8);
+  p += 8;
+  for (auto& m : c->mem) {
+    for (auto [src, n] : {std::pair<const void*, size_t>{m.rs, m.rs_bytes}, {m.inlet, m.inlet_bytes},
+                          {m.lat, m.lat_bytes}}) {
+      e = cudaMemcpy(p, src, n, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
+      p += n;
+    }
+  }
+  *bytes = need;
+  return read_flags(c, -1, nullptr);
+}
+
+int vlbm_load(vlbm_ctx* c, const void* host_buf, size_t bytes) {
+  if (!c || !host_buf) return fail(c, VLBM_EINVAL, "ctx and host_buf are required");
+  if (!c->initialized) return fail(c, VLBM_ESTATE, "call vlbm_init_ensemble with the same M before vlbm_load");
+  size_t need = 5 * sizeof(uint32_t) + 8;
+  for (auto& m : c->mem) need += m.rs_bytes + m.inlet_bytes + m.lat_bytes;
+  if (bytes != need) return fail(c, VLBM_EINVAL, "checkpoint size does not match this context");
+  const unsigned char* p = static_cast<const unsigned char*>(host_buf);
+  uint32_t hdr[5];
+  std::memcpy(hdr, p, sizeof(hdr));
+  if (hdr[0] != kSaveMagic || hdr[1] != kSaveVersion || hdr[2] != (uint32_t)c->precision ||
+      hdr[3] != (uint32_t)c->grids.size() || hdr[4] != (uint32_t)c->M)
+    return fail(c, VLBM_EINVAL, "checkpoint header does not match this context");
+  p += sizeof(hdr) + 8;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  for (auto& m : c->mem) {
+    for (auto [dst, n] : {std::pair<void*, size_t>{m.rs, m.rs_bytes}, {m.inlet, m.inlet_bytes},
+                          {m.lat, m.lat_bytes}}) {
+      e = cudaMemcpy(dst, p, n, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint restore");
+      p += n;
+    }
+  }
+  c->prepared = false;
+  return VLBM_OK;
+}
+
+unsigned long long vlbm_kernel_launches(void) { return g_launches.load(); }
+
+const char* vlbm_last_error(const vlbm_ctx* c) { return c ? c->err.c_str() : g_thread_error.c_str(); }
+
+void vlbm_destroy(vlbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  release_levels(c);
+  dev_free(c, c->d_count);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

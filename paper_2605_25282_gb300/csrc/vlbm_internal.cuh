@@ -1,0 +1,119 @@
+// Internal declarations of libvlbm (not part of the public C ABI).
+//
+// Device layout of one level (per realization m, lattice L in {0, 1}):
+//   VLBM_FP64 : 20 planes of double [ny][nx_pad]:
+//               planes 0..3   conserved u = (rho, rho v1, rho v2, E)
+//               planes 4..19  raw populations u_k, plane 4 + 4(k-1) + c
+//   VLBM_MIXED: 5 planes of float4 [ny][nx_pad]:
+//               plane 0       nodal state (rho, v1, v2, p)
+//               planes 1..4   non-equilibrium part of population k = 1..4,
+//                             (rho, m1, m2, E)-components, boosted into the
+//                             node's rest frame (velocity = stored v)
+// Lattice L of realization m starts at  base + (L * M + m) * real_stride.
+// The two lattices ping-pong per realization with the parity of its own step
+// count, so realizations that stop early (landing) keep a consistent state.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/vlbm.h"
+
+namespace vlbm {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMaxModes = 16;
+
+// Per (level, realization) bookkeeping, device resident.
+struct RealState {
+  double t;            // time t_n of the current state
+  double t_target;     // landing target (+inf for fixed step counts)
+  double a;            // kinetic speed a_n of the pending step
+  double inv2a;        // 0.5 / a_n
+  double dt;           // dx / a_n (or t_target - t_n when landing)
+  double inv2a_prev;   // MIXED: the 1/(2a) the stored non-equilibrium parts refer to
+  float inv2a_f;       // MIXED: 1/(2a_n) rounded down to FP32 (a_eff >= a_n)
+  float dinv2a_f;      // MIXED: inv2a_prev - inv2a_f, the correction of the stored parts
+  long long steps;     // steps taken; lattice parity = steps & 1
+  unsigned long long lam_bits;       // lambda(u^n) as ordered bits of a non-negative double
+  unsigned long long lam_next_bits;  // lambda(u^{n+1}) accumulated by the running step
+  int active;          // the pending step runs for this realization
+  int landing;         // the pending step lands on t_target
+  int flags;           // sticky: 1 non-positive, 2 non-finite
+  int gref_set;        // MIXED: inv2a_prev is valid
+};
+
+struct LevelDesc {
+  int nx, ny, nx_pad;
+  int tiles_x, tiles_y;
+  int tile_begin;        // first flattened tile index of this level in a step launch
+  double dx, y_min;
+  size_t plane;          // elements per plane (ny * nx_pad)
+  size_t real_stride;    // elements (double or float4) per realization and lattice
+  void* lat;             // lattice storage base
+  double* inlet;         // [M][4][ny] conserved inlet state (FP64)
+  RealState* rs;         // [M]
+};
+
+struct Physics {
+  double gamma, alpha, kappa;
+  int limiter;
+  double rlmp_rel, rlmp_abs, eps_pos;
+  double jet_rho, jet_u, jet_v, jet_p;
+  double amb_rho, amb_u, amb_v, amb_p;
+};
+
+struct Launch {
+  Physics ph;
+  int nlevels;
+  int M;
+  int total_tiles;
+  LevelDesc lv[kMaxLevels];
+};
+
+// Ordered bits of a non-negative double (monotone as unsigned integers).
+__host__ __device__ inline unsigned long long lam_to_bits(double x) {
+  union {
+    double d;
+    unsigned long long u;
+  } c;
+  c.d = x;
+  return c.u;
+}
+__host__ __device__ inline double bits_to_lam(unsigned long long b) {
+  union {
+    double d;
+    unsigned long long u;
+  } c;
+  c.u = b;
+  return c.d;
+}
+
+// Counts kernel launches enqueued by the library (see vlbm_kernel_launches).
+void add_launches(unsigned n);
+
+// Launch helpers implemented in the kernel translation units.
+cudaError_t launch_step_f64(const Launch& L, cudaStream_t s);
+cudaError_t launch_step_mixed(const Launch& L, cudaStream_t s);
+size_t step_f64_smem_bytes();
+size_t step_mixed_smem_bytes();
+
+cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, cudaStream_t s);
+cudaError_t launch_init_state(const Launch& L, int precision, cudaStream_t s);
+cudaError_t launch_lambda(const Launch& L, int precision, int level, int m0, int count, cudaStream_t s);
+cudaError_t launch_fill_equilibrium_f64(const Launch& L, int level, int m0, int count, cudaStream_t s);
+cudaError_t launch_tick(const Launch& L, int precision, int advance, cudaStream_t s);
+cudaError_t launch_set_target(const Launch& L, double t_target, cudaStream_t s);
+cudaError_t launch_moments(const Launch& L, int precision, int level, int m0, int count, double* rho,
+                           double* u, double* v, double* p, cudaStream_t s);
+cudaError_t launch_density(const Launch& L, int precision, int level, int m0, int count, void* rho,
+                           int as_f32, cudaStream_t s);
+cudaError_t launch_get_state(const Launch& L, int precision, int level, int m0, int count, double* u,
+                             double* pops, cudaStream_t s);
+cudaError_t launch_set_state(const Launch& L, int precision, int level, int m0, int count, const double* u,
+                             const double* pops, cudaStream_t s);
+cudaError_t launch_count_active(const Launch& L, int* d_count, cudaStream_t s);
+
+}  // namespace vlbm

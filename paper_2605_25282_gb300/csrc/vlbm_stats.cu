@@ -1,0 +1,151 @@
+// Per-cell ensemble statistics between two grid levels (Sec. 3.2 restriction,
+// Sec. 3.4 Eqs. (mean), (std), (w1disc)).
+//
+// One CTA per coarse cell.  The M samples of ensemble a and the M restricted
+// samples of ensemble b (each realization of b block-averaged over its r x r
+// fine cells onto the coarse cell) are gathered into shared memory, padded to
+// a power of two with +inf, bitonic-sorted, and reduced in FP64:
+//   mean = sum / M, std = sqrt(sum (x - mean)^2 / M)  (population variance),
+//   W1   = sum_m |a_(m) - b_(m)| / M  over the ascending order statistics.
+// The gather is strided by the field size; consecutive CTAs are neighbouring
+// cells, so the rest of each 32-byte sector is reused from L2.
+#include "vlbm_internal.cuh"
+
+namespace vlbm {
+namespace {
+
+constexpr int kStatThreads = 256;
+
+__device__ __forceinline__ double load_sample(const void* p, int is_f32, size_t idx) {
+  return is_f32 ? (double)reinterpret_cast<const float*>(p)[idx] : reinterpret_cast<const double*>(p)[idx];
+}
+
+__device__ void bitonic_sort(double* x, int P) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+        const int lo = 2 * j * (t / j) + (t % j);
+        const int hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const double a = x[lo], b = x[hi];
+        if ((a > b) == up) {
+          x[lo] = b;
+          x[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+__global__ void __launch_bounds__(kStatThreads) stats_kernel(const void* __restrict__ ens_a, int a_f32, int nxa,
+                                                             int nya, const void* __restrict__ ens_b, int b_f32,
+                                                             int nxb, int r, int M, int P, double* mean_a,
+                                                             double* std_a, double* mean_b, double* std_b,
+                                                             double* w1) {
+  extern __shared__ double sm[];
+  double* xa = sm;
+  double* xb = sm + P;
+  __shared__ double red[kStatThreads / 32];
+  const int cell = blockIdx.x;
+  const int I = cell % nxa, J = cell / nxa;
+  const size_t na = (size_t)nxa * nya;
+  const size_t nb = na * (size_t)r * r;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  for (int m = threadIdx.x; m < P; m += blockDim.x) {
+    if (m < M) {
+      xa[m] = load_sample(ens_a, a_f32, (size_t)m * na + cell);
+      double s = 0.0;
+      for (int aa = 0; aa < r; ++aa)
+        for (int bb = 0; bb < r; ++bb)
+          s += load_sample(ens_b, b_f32, (size_t)m * nb + (size_t)(r * J + aa) * nxb + (size_t)(r * I + bb));
+      xb[m] = s / (double)(r * r);
+    } else {
+      xa[m] = inf;
+      xb[m] = inf;
+    }
+  }
+  __syncthreads();
+  // moments (before sorting; order-independent up to round-off)
+  double sa = 0.0, sb = 0.0;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    sa += xa[m];
+    sb += xb[m];
+  }
+  const double ma = block_sum(sa, red) / (double)M;
+  const double mb = block_sum(sb, red) / (double)M;
+  double va = 0.0, vb = 0.0;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    const double da = xa[m] - ma, db = xb[m] - mb;
+    va += da * da;
+    vb += db * db;
+  }
+  const double vA = block_sum(va, red) / (double)M;
+  const double vB = block_sum(vb, red) / (double)M;
+  __syncthreads();
+  bitonic_sort(xa, P);
+  bitonic_sort(xb, P);
+  double w = 0.0;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) w += fabs(xa[m] - xb[m]);
+  const double W = block_sum(w, red) / (double)M;
+  if (threadIdx.x == 0) {
+    if (mean_a) mean_a[cell] = ma;
+    if (std_a) std_a[cell] = sqrt(vA);
+    if (mean_b) mean_b[cell] = mb;
+    if (std_b) std_b[cell] = sqrt(vB);
+    if (w1) w1[cell] = W;
+  }
+}
+
+}  // namespace
+
+int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32, int nxb,
+                 int nyb, int M, double* mean_a, double* std_a, double* mean_b, double* std_b, double* w1,
+                 cudaStream_t s, const char** why) {
+  if (!ens_a || !ens_b) {
+    *why = "ensemble pointers must be non-NULL";
+    return VLBM_EINVAL;
+  }
+  if (nxa < 1 || nya < 1 || M < 1 || M > 4096) {
+    *why = "need nxa, nya >= 1 and 1 <= M <= 4096";
+    return VLBM_EINVAL;
+  }
+  if (nxb % nxa != 0 || nyb % nya != 0 || nxb / nxa != nyb / nya) {
+    *why = "ensemble b must be an integer refinement (same factor in x and y) of ensemble a";
+    return VLBM_EINVAL;
+  }
+  const int r = nxb / nxa;
+  int P = 1;
+  while (P < M) P <<= 1;
+  const size_t smem = 2 * (size_t)P * sizeof(double);
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8) !=
+        cudaSuccess) {
+      *why = "cudaFuncSetAttribute failed for the statistics kernel";
+      return VLBM_ECUDA;
+    }
+    configured = true;
+  }
+  stats_kernel<<<nxa * nya, kStatThreads, smem, s>>>(ens_a, a_is_f32, nxa, nya, ens_b, b_is_f32, nxb, r, M, P,
+                                                     mean_a, std_a, mean_b, std_b, w1);
+  add_launches(1);
+  if (cudaGetLastError() != cudaSuccess) {
+    *why = "statistics kernel launch failed";
+    return VLBM_ECUDA;
+  }
+  return VLBM_OK;
+}
+
+}  // namespace vlbm

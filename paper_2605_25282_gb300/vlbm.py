@@ -1,0 +1,343 @@
+"""Python binding of libvlbm (ctypes; argument marshalling only).
+
+Every step of the method runs in the CUDA library; PyTorch provides device
+memory (its caching allocator backs the library's state) and the stream.  The
+binding never falls back to a CPU path: it raises if the library or a GPU is
+missing.
+
+Names follow the C ABI in include/vlbm.h: ``Ensemble`` wraps a ``vlbm_ctx``
+(vlbm_create / vlbm_init_ensemble / vlbm_step / vlbm_advance_to / vlbm_moments
+...), and ``stats_w1_mean_std`` wraps the statistics call.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+VLBM_FP64, VLBM_MIXED = 0, 1
+LIMITER_NONE, LIMITER_UNLIMITED, LIMITER_RTHETA = 0, 1, 2
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONPOSITIVE", 5: "ENONFINITE", 6: "ETIMEOUT",
+          7: "ESTATE"}
+
+EXPORTED = [
+    "vlbm_default_relax", "vlbm_default_perturb", "vlbm_create", "vlbm_init_ensemble",
+    "vlbm_init_ensemble_block", "vlbm_kernel_launches", "vlbm_step",
+    "vlbm_advance_to", "vlbm_moments", "vlbm_density", "vlbm_time", "vlbm_sync", "vlbm_get_state",
+    "vlbm_set_state", "stats_w1_mean_std", "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_destroy",
+]
+
+
+class VlbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x_max", ctypes.c_double),
+                ("y_min", ctypes.c_double), ("y_max", ctypes.c_double)]
+
+
+class Prim(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("u", ctypes.c_double), ("v", ctypes.c_double),
+                ("p", ctypes.c_double)]
+
+
+class Relax(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("kappa", ctypes.c_double), ("limiter", ctypes.c_int),
+                ("rlmp_rel", ctypes.c_double), ("rlmp_abs", ctypes.c_double), ("eps_pos", ctypes.c_double)]
+
+
+class Perturb(ctypes.Structure):
+    _fields_ = [("r_jet", ctypes.c_double), ("A", ctypes.c_double), ("p_decay", ctypes.c_double),
+                ("K", ctypes.c_int), ("amp", ctypes.c_double * 16), ("use_amp", ctypes.c_int)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads libvlbm.so (building it with nvcc when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libvlbm not built: {_build.LIB} is missing (run paper_2605_25282_gb300/build.py)")
+    lib = ctypes.CDLL(_build.LIB)
+    p, i, d, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+    sig = {
+        "vlbm_default_relax": ([p], None),
+        "vlbm_default_perturb": ([p], None),
+        "vlbm_create": ([p, i, d, p, p, p, i, p, ALLOC_FN, FREE_FN, p, ctypes.POINTER(p)], i),
+        "vlbm_init_ensemble": ([p, u64, i, p], i),
+        "vlbm_init_ensemble_block": ([p, u64, i, i, p], i),
+        "vlbm_kernel_launches": ([], ctypes.c_ulonglong),
+        "vlbm_step": ([p, i], i),
+        "vlbm_advance_to": ([p, d], i),
+        "vlbm_moments": ([p, i, i, i, p, p, p, p], i),
+        "vlbm_density": ([p, i, i, i, p, i], i),
+        "vlbm_time": ([p, i, p, p], i),
+        "vlbm_sync": ([p], i),
+        "vlbm_get_state": ([p, i, i, i, p, p], i),
+        "vlbm_set_state": ([p, i, i, i, p, p], i),
+        "stats_w1_mean_std": ([p, i, i, i, p, i, i, i, i, p, p, p, p, p, p], i),
+        "vlbm_save": ([p, p, ctypes.POINTER(ctypes.c_size_t)], i),
+        "vlbm_load": ([p, p, ctypes.c_size_t], i),
+        "vlbm_last_error": ([p], ctypes.c_char_p),
+        "vlbm_destroy": ([p], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(code: int, ctx=None):
+    if code != 0:
+        msg = load_library().vlbm_last_error(ctx).decode()
+        raise VlbmError(code, msg)
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("libvlbm needs a CUDA GPU; no CPU fallback exists")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def jet_grid(nx: int, ny: int, x_max: float = 2.5) -> Grid:
+    """Square cells of size x_max / nx on [0, x_max] x [-ny dx / 2, ny dx / 2]."""
+    dx = x_max / nx
+    return Grid(nx, ny, x_max, -0.5 * ny * dx, 0.5 * ny * dx)
+
+
+@dataclass
+class JetProblem:
+    """Sec. 2.2 constants of the Mach 2000 jet."""
+    gamma: float = 5.0 / 3.0
+    rho_jet: float = 5.0
+    v_jet: float = 800.0
+    p_amb: float = 0.4127
+    rho_amb: float = 0.5
+
+
+@dataclass
+class PerturbParams:
+    """Sec. 2.3, Eq. (karhunenExp)."""
+    r_jet: float = 0.05
+    A: float = 0.1
+    p_decay: float = 2.0
+    K: int = 10
+    amp: list | None = None
+
+    def c(self) -> Perturb:
+        p = Perturb()
+        p.r_jet, p.A, p.p_decay, p.K = self.r_jet, self.A, self.p_decay, self.K
+        if self.amp is not None:
+            for k, a in enumerate(self.amp):
+                p.amp[k] = float(a)
+            p.use_amp = 1
+        return p
+
+
+@dataclass
+class RelaxParams:
+    alpha: float = 0.0
+    kappa: float = 1.0
+    limiter: int = LIMITER_RTHETA
+    rlmp_rel: float = 0.1
+    rlmp_abs: float = 0.0
+    eps_pos: float = 1e-13
+
+    def c(self) -> Relax:
+        return Relax(self.alpha, self.kappa, self.limiter, self.rlmp_rel, self.rlmp_abs, self.eps_pos)
+
+
+class Ensemble:
+    """A Monte-Carlo ensemble of jet realizations on one or more grid levels."""
+
+    def __init__(self, levels, precision: str = "fp64", problem: JetProblem = JetProblem(),
+                 relax: RelaxParams = RelaxParams(), stream: torch.cuda.Stream | None = None,
+                 device: int | None = None):
+        _require_cuda()
+        self.lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.grids = [lv if isinstance(lv, Grid) else jet_grid(*lv) for lv in levels]
+        self.precision = {"fp64": VLBM_FP64, "mixed": VLBM_MIXED}[precision]
+        self.problem = problem
+        # The context needs a real stream: PyTorch's default stream has handle 0,
+        # which the C ABI would read as "create a private stream".
+        if stream is None or stream.cuda_stream == 0:
+            stream = torch.cuda.Stream(self.device)
+        self.stream = stream
+        blocks = {}
+        self._blocks = blocks
+        dev_index, alloc_stream = self.device.index, self.stream
+
+        # The callbacks hold no reference to self, so the ensemble is freed as
+        # soon as it is unreachable (no reference cycle through ctypes).
+        def _alloc(nbytes, _user):
+            with torch.cuda.device(dev_index):
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), dev_index, alloc_stream)
+            blocks[ptr] = nbytes
+            return ptr
+
+        def _free(ptr, _user):
+            if ptr in blocks:
+                del blocks[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        arr = (Grid * len(self.grids))(*self.grids)
+        jet = Prim(problem.rho_jet, problem.v_jet, 0.0, problem.p_amb)
+        amb = Prim(problem.rho_amb, 0.0, 0.0, problem.p_amb)
+        rel = relax.c()
+        ctx = ctypes.c_void_p()
+        _check(self.lib.vlbm_create(arr, len(self.grids), problem.gamma, ctypes.byref(jet), ctypes.byref(amb),
+                                    ctypes.byref(rel), self.precision, ctypes.c_void_p(self.stream.cuda_stream),
+                                    self._alloc_cb, self._free_cb, None, ctypes.byref(ctx)))
+        self.ctx = ctx
+        self.M = 0
+
+    def _enter(self):
+        """Orders the context's stream after work already queued by the caller."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            self.stream.wait_stream(cur)
+
+    def _leave(self):
+        """Orders the caller's current stream after the context's work."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self.stream.cuda_stream:
+            cur.wait_stream(self.stream)
+
+    def _call(self, fn, *args):
+        self._enter()
+        code = fn(self.ctx, *args)
+        self._leave()
+        _check(code, self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.vlbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, level: int):
+        g = self.grids[level]
+        return g.ny, g.nx
+
+    def init(self, seed: int, M: int, perturb: PerturbParams = PerturbParams(), m_begin: int = 0):
+        p = perturb.c()
+        self._call(self.lib.vlbm_init_ensemble_block, seed, m_begin, M, ctypes.byref(p))
+        self.M = M
+
+    def step(self, n: int = 1):
+        self._call(self.lib.vlbm_step, n)
+
+    def advance_to(self, t: float):
+        self._call(self.lib.vlbm_advance_to, float(t))
+
+    def _count(self, m0, count):
+        return self.M - m0 if count is None else count
+
+    def moments(self, level: int = 0, m0: int = 0, count: int | None = None):
+        count = self._count(m0, count)
+        ny, nx = self.shape(level)
+        out = [torch.empty((count, ny, nx), dtype=torch.float64, device=self.device) for _ in range(4)]
+        self._call(self.lib.vlbm_moments, level, m0, count, *[_ptr(o) for o in out])
+        return dict(zip(("rho", "u", "v", "p"), out))
+
+    def density(self, level: int = 0, m0: int = 0, count: int | None = None, f32: bool = True,
+                out: torch.Tensor | None = None):
+        count = self._count(m0, count)
+        ny, nx = self.shape(level)
+        if out is None:
+            out = torch.empty((count, ny, nx), dtype=torch.float32 if f32 else torch.float64, device=self.device)
+        self._call(self.lib.vlbm_density, level, m0, count, _ptr(out), int(out.dtype == torch.float32))
+        return out
+
+    def time(self, level: int = 0):
+        t = np.zeros(self.M)
+        s = np.zeros(self.M, dtype=np.int64)
+        self._call(self.lib.vlbm_time, level, t.ctypes.data_as(ctypes.c_void_p), s.ctypes.data_as(ctypes.c_void_p))
+        return t, s
+
+    def sync(self):
+        self._call(self.lib.vlbm_sync)
+
+    def get_state(self, level: int = 0, m0: int = 0, count: int | None = None, pops: bool = True):
+        count = self._count(m0, count)
+        ny, nx = self.shape(level)
+        u = torch.empty((count, 4, ny, nx), dtype=torch.float64, device=self.device)
+        f = torch.empty((count, 16, ny, nx), dtype=torch.float64, device=self.device) if pops else None
+        self._call(self.lib.vlbm_get_state, level, m0, count, _ptr(u), _ptr(f))
+        return u, f
+
+    def set_state(self, u: torch.Tensor, pops: torch.Tensor, level: int = 0, m0: int = 0):
+        u = u.to(self.device, torch.float64).contiguous()
+        pops = pops.to(self.device, torch.float64).contiguous()
+        count = u.shape[0]
+        self._call(self.lib.vlbm_set_state, level, m0, count, _ptr(u), _ptr(pops))
+        self._keep = (u, pops)
+
+    def save(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        self._call(self.lib.vlbm_save, None, ctypes.byref(n))
+        buf = (ctypes.c_ubyte * n.value)()
+        self._call(self.lib.vlbm_save, buf, ctypes.byref(n))
+        return bytes(buf)
+
+    def load(self, blob: bytes):
+        buf = (ctypes.c_ubyte * len(blob)).from_buffer_copy(blob)
+        self._call(self.lib.vlbm_load, buf, len(blob))
+
+
+def kernel_launches() -> int:
+    """Kernels enqueued by libvlbm in this process so far."""
+    return int(load_library().vlbm_kernel_launches())
+
+
+def stats_w1_mean_std(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cuda.Stream | None = None):
+    """Per-cell mean/std of both ensembles and one-point W1 (b restricted onto a's grid)."""
+    _require_cuda()
+    lib = load_library()
+    if ens_a.dim() != 3 or ens_b.dim() != 3 or ens_a.shape[0] != ens_b.shape[0]:
+        raise ValueError("ensembles must be [M, ny, nx] with equal M")
+    ens_a = ens_a.contiguous()
+    ens_b = ens_b.contiguous()
+    M, nya, nxa = ens_a.shape
+    _, nyb, nxb = ens_b.shape
+    dev = ens_a.device
+    out = [torch.empty((nya, nxa), dtype=torch.float64, device=dev) for _ in range(5)]
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    _check(lib.stats_w1_mean_std(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
+                                 int(ens_b.dtype == torch.float32), nxb, nyb, M, *[_ptr(o) for o in out],
+                                 ctypes.c_void_p(s.cuda_stream)))
+    return dict(zip(("mean_a", "std_a", "mean_b", "std_b", "w1"), out))

@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads and exports every call include/vlbm.h
+declares; host-side validation rejects bad arguments before any device work.
+These tests make no compute call and need no GPU."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2605_25282_gb300 import vlbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "vlbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = "\n".join(l for l in src.splitlines() if "typedef" not in l)
+    names = re.findall(r"\b((?:vlbm|stats)_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declarations_are_exported():
+    names = declared_functions()
+    assert "vlbm_create" in names and "stats_w1_mean_std" in names
+    assert sorted(vlbm.EXPORTED) == names
+    lib = vlbm.load_library()
+    out = subprocess.run(["nm", "-D", "--defined-only", vlbm.library_path()], capture_output=True, text=True).stdout
+    syms = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    for n in names:
+        assert n in syms, n
+        assert getattr(lib, n) is not None
+
+
+def _create(levels, gamma=5 / 3, jet=None, amb=None, relax=None, precision=0):
+    lib = vlbm.load_library()
+    arr = (vlbm.Grid * max(1, len(levels)))(*levels) if levels else None
+    jet = jet or vlbm.Prim(5.0, 800.0, 0.0, 0.4127)
+    amb = amb or vlbm.Prim(0.5, 0.0, 0.0, 0.4127)
+    ctx = ctypes.c_void_p()
+    rel = ctypes.byref(relax) if relax is not None else None
+    code = lib.vlbm_create(arr, len(levels), gamma, ctypes.byref(jet), ctypes.byref(amb), rel, precision, None,
+                           vlbm.ALLOC_FN(0), vlbm.FREE_FN(0), None, ctypes.byref(ctx))
+    return code, lib.vlbm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case, expect", [
+    (dict(levels=[]), "1..8 grid levels"),
+    (dict(levels=[vlbm.Grid(2, 100, 2.5, -0.625, 0.625)]), "nx, ny >= 3"),
+    (dict(levels=[vlbm.Grid(200, 100, 2.5, -0.5, 0.5)]), "square"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], gamma=1.0), "gamma"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], jet=vlbm.Prim(-5.0, 800.0, 0.0, 0.4127)), "rho > 0"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], precision=7), "precision"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(1.0, 1.0, 2, 0.1, 0.0, 1e-13)), "alpha"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(0.0, 0.5, 2, 0.1, 0.0, 1e-13)), "kappa"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(0.0, 1.0, 5, 0.1, 0.0, 1e-13)), "limiter"),
+])
+def test_create_rejects_invalid_problems(case, expect):
+    code, msg = _create(**case)
+    assert code == 1, (code, msg)
+    assert expect in msg
+
+
+def test_stats_rejects_bad_shapes_without_launching():
+    lib = vlbm.load_library()
+    dummy = ctypes.c_void_p(16)
+    # b is not an integer refinement of a
+    code = lib.stats_w1_mean_std(dummy, 0, 10, 10, dummy, 0, 15, 15, 4, None, None, None, None, None, None)
+    assert code == 1 and "refinement" in lib.vlbm_last_error(None).decode()
+    code = lib.stats_w1_mean_std(dummy, 0, 10, 10, dummy, 0, 20, 30, 4, None, None, None, None, None, None)
+    assert code == 1
+    code = lib.stats_w1_mean_std(dummy, 0, 10, 10, dummy, 0, 10, 10, 5000, None, None, None, None, None, None)
+    assert code == 1 and "M" in lib.vlbm_last_error(None).decode()
+    code = lib.stats_w1_mean_std(None, 0, 10, 10, dummy, 0, 10, 10, 4, None, None, None, None, None, None)
+    assert code == 1
+
+
+def test_null_context_calls_fail_cleanly():
+    lib = vlbm.load_library()
+    assert lib.vlbm_step(None, 1) == 1
+    assert lib.vlbm_advance_to(None, 0.1) == 1
+    assert lib.vlbm_sync(None) == 1
+    assert lib.vlbm_last_error(None)
+    lib.vlbm_destroy(None)

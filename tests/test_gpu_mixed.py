@@ -1,0 +1,65 @@
+"""Mixed path (FP32 storage, rest-frame FP32 arithmetic) against the FP64 oracle.
+
+Short horizon, per cell: the FP32 state carries ~6e-8 relative rounding per
+step; over 10 steps and the jet's amplification the bound below is what the
+FP32 arithmetic allows (derivation in the comparison norms' docstring).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+RTOL32 = 2e-4
+
+
+def mixed_errors(nx, ny, M, n, limiter=2):
+    ref = H.oracle_jet(nx, ny, M, n, limiter=limiter)
+    ens = H.gpu_jet([(nx, ny)], M, precision="mixed", limiter=limiter)
+    ens.step(n)
+    mo = {k: H.to_np(v) for k, v in ens.moments(0).items()}
+    g = O.Grid(nx, ny)
+    out = {"rho": 0.0, "v": 0.0, "p": 0.0}
+    for m in range(M):
+        rho, v1, v2, p = O.moments(g, H.oracle_params(limiter), ref["u"][m])
+        c = np.sqrt(5.0 / 3.0 * p / rho)
+        out["rho"] = max(out["rho"], (np.abs(mo["rho"][m] - rho) / rho).max())
+        out["p"] = max(out["p"], (np.abs(mo["p"][m] - p) / p).max())
+        vs = np.abs(v1) + np.abs(v2) + c
+        out["v"] = max(out["v"], (np.maximum(np.abs(mo["u"][m] - v1), np.abs(mo["v"][m] - v2)) / vs).max())
+    t, s = ens.time(0)
+    out["t"] = np.abs(t - ref["t"]).max() / ref["t"].max()
+    return out
+
+
+@pytest.mark.parametrize("limiter", [2, 0])
+def test_mixed_jet_10_steps(limiter):
+    e = mixed_errors(200, 100, 4, 10, limiter)
+    print("mixed vs FP64 oracle after 10 steps:", e)
+    assert e["rho"] <= RTOL32 and e["p"] <= RTOL32 and e["v"] <= RTOL32, e
+    assert e["t"] <= 1e-6
+
+
+def test_mixed_ragged_multilevel():
+    levels = [(67, 29), (134, 58)]
+    ens = H.gpu_jet(levels, 2, precision="mixed")
+    ens.step(6)
+    for l, (nx, ny) in enumerate(levels):
+        ref = H.oracle_jet(nx, ny, 2, 6)
+        mo = {k: H.to_np(v) for k, v in ens.moments(l).items()}
+        g = O.Grid(nx, ny)
+        for m in range(2):
+            rho, v1, v2, p = O.moments(g, H.oracle_params(), ref["u"][m])
+            assert (np.abs(mo["rho"][m] - rho) / rho).max() <= RTOL32
+            assert (np.abs(mo["p"][m] - p) / p).max() <= RTOL32
+
+
+def test_mixed_positivity_over_smallest_config():
+    ens = H.gpu_jet([(200, 100)], 4, precision="mixed")
+    ens.step(500)
+    ens.sync()
+    mo = ens.moments(0)
+    assert float(mo["rho"].min()) > 0 and float(mo["p"].min()) > 0

@@ -1,0 +1,59 @@
+"""GPU statistics kernel (through stats_w1_mean_std) against the oracle's
+restriction + mean / population std / one-point W1 (Sec. 3.2, Sec. 3.4).
+
+Sums of M values in a different order differ by ~M eps: the bar is 1e-12
+relative to the cell's scale (the sample magnitude).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2605_25282_gb300 import vlbm
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def run(a, b, f32=False):
+    dt = torch.float32 if f32 else torch.float64
+    ta = torch.tensor(a, dtype=dt, device="cuda")
+    tb = torch.tensor(b, dtype=dt, device="cuda")
+    out = vlbm.stats_w1_mean_std(ta, tb)
+    torch.cuda.synchronize()
+    if f32:
+        a = ta.double().cpu().numpy()
+        b = tb.double().cpu().numpy()
+    ref = O.stats_w1_mean_std(a, b)
+    return {k: v.cpu().numpy() for k, v in out.items()}, ref, a
+
+
+@pytest.mark.parametrize("M", [1, 2, 7, 64, 1000, 4096])
+@pytest.mark.parametrize("r", [1, 2])
+def test_stats_match_oracle(M, r):
+    ny, nx = (13, 7) if M < 1000 else (4, 6)
+    a = inputs.random_samples(1, M, ny, nx)
+    b = inputs.random_samples(2, M, r * ny, r * nx)
+    got, ref, _ = run(a, b)
+    scale = np.abs(a).max()
+    for key, rv in zip(("mean_a", "std_a", "mean_b", "std_b", "w1"), ref):
+        assert np.abs(got[key] - rv).max() <= 1e-12 * scale, key
+
+
+@pytest.mark.parametrize("dist", ["lognormal", "ties"])
+def test_stats_fp32_inputs_and_ties(dist):
+    a = inputs.random_samples(3, 33, 5, 9, dist)
+    b = inputs.random_samples(4, 33, 20, 36, dist)
+    got, ref, a64 = run(a, b, f32=True)
+    scale = np.abs(a64).max()
+    for key, rv in zip(("mean_a", "std_a", "mean_b", "std_b", "w1"), ref):
+        assert np.abs(got[key] - rv).max() <= 1e-12 * scale, key
+
+
+def test_stats_identical_ensembles_and_shift():
+    a = inputs.random_samples(5, 100, 6, 6)
+    got, _, _ = run(a, a)
+    assert np.all(got["w1"] == 0) and np.array_equal(got["mean_a"], got["mean_b"])
+    got, _, _ = run(a, a + 0.5)
+    assert np.allclose(got["w1"], 0.5, rtol=1e-12)
