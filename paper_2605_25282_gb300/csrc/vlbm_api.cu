@@ -354,6 +354,14 @@ int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, con
   Launch& L = c->launch;
   L = Launch{};
   L.ph = c->ph;
+  L.pf.gamma = (float)c->ph.gamma;
+  L.pf.gm1 = (float)(c->ph.gamma - 1.0);
+  L.pf.rg = (float)(1.0 / (c->ph.gamma - 1.0));
+  L.pf.alpha = (float)c->ph.alpha;
+  L.pf.c1 = (float)((1.0 - c->ph.alpha) / 4.0);
+  L.pf.rel = (float)c->ph.rlmp_rel;
+  L.pf.absb = (float)c->ph.rlmp_abs;
+  L.pf.eps = (float)c->ph.eps_pos;
   L.nlevels = (int)c->grids.size();
   L.M = M;
   int tiles = 0;

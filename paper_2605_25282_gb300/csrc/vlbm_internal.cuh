@@ -65,8 +65,17 @@ struct Physics {
   double amb_rho, amb_u, amb_v, amb_p;
 };
 
+// FP32 constants of the mixed kernel, rounded once on the host so the kernel
+// issues no FP64 instruction (GB300's FP64 pipe runs at 1/58 of FP32).
+struct PhysicsF32 {
+  float gamma, gm1, rg;  // gamma, gamma - 1, 1 / (gamma - 1)
+  float alpha, c1;       // alpha, (1 - alpha) / 4
+  float rel, absb, eps;  // rlmp_rel, rlmp_abs, eps_pos
+};
+
 struct Launch {
   Physics ph;
+  PhysicsF32 pf;
   int nlevels;
   int M;
   int total_tiles;

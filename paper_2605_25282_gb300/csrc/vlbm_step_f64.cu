@@ -8,9 +8,11 @@
 //       the relaxed local density bounds of every node of tile + 1 halo
 //   P3  every face touching the tile: d_f, blending parameter theta_f
 //       (R-theta limiter), and the two streamed populations it owns
-//   P4  every tile node: u^{n+1} = U_LF + sum_f s theta_f d_f (Eq. (vlbm5)
-//       regrouped per face), zero-gradient copies, inlet column, lambda for
-//       the next kinetic speed (block max + one atomicMax per CTA).
+//   P4  every tile node: u^{n+1} by Eq. (vlbm5) in the order it is written,
+//       zero-gradient copies, inlet column, lambda for the next kinetic speed
+//       (block max + one atomicMax per CTA).
+// The translation unit is compiled without FMA contraction and evaluates every
+// expression in the oracle's order, so the two agree to round-off.
 // FP64 is the slow path on GB300 (1/58 of the FP32 rate): this kernel is
 // bound by the FP64 pipe, not by HBM.
 #include <cfloat>
@@ -30,10 +32,12 @@ struct Smem {
   double g[4][HY][HX];
   double ulf[4][GY][GX];
   double bnd[4][GY][GX];  // lo_b, hi_b, eps_rho, eps_p
+  // per face: theta, the two non-equilibrium terms M_out(u_L) - u_out,L and
+  // M_in(u_R) - u_in,R, and the two streamed populations of Eqs. (vlbm1)-(vlbm4)
   double thx[TY][TX + 1];
   double thy[TY + 1][TX];
-  double dx[4][TY][TX + 1];
-  double dy[4][TY + 1][TX];
+  double eox[4][TY][TX + 1], eix[4][TY][TX + 1], nox[4][TY][TX + 1], nix[4][TY][TX + 1];
+  double eoy[4][TY + 1][TX], eiy[4][TY + 1][TX], noy[4][TY + 1][TX], niy[4][TY + 1][TX];
   unsigned long long lam[NT / 32];
   int flags[NT / 32];
 };
@@ -120,7 +124,7 @@ __device__ __forceinline__ void write_equilibrium_node(double* dst, size_t plane
   }
 }
 
-__global__ void __launch_bounds__(NT, 2) step_f64_kernel(const Launch L) {
+__global__ void __launch_bounds__(NT, 1) step_f64_kernel(const Launch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& S = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x;
@@ -278,23 +282,39 @@ __global__ void __launch_bounds__(NT, 2) step_f64_kernel(const Launch L) {
       }
       th = tL < tR ? tL : tR;
     }
+    // streamed populations owned by this face (Eqs. (vlbm1)-(vlbm4))
+    double no[4], ni[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      no[c] = Mo[c] + th * (Mo[c] - pL[c]);
+      ni[c] = Mi[c] + th * (Mi[c] - pR[c]);
+    }
     if (xdir) {
       S.thx[fb][fa] = th;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) S.dx[c][fb][fa] = d[c];
+      for (int c = 0; c < 4; ++c) {
+        S.eox[c][fb][fa] = Mo[c] - pL[c];
+        S.eix[c][fb][fa] = Mi[c] - pR[c];
+        S.nox[c][fb][fa] = no[c];
+        S.nix[c][fb][fa] = ni[c];
+      }
     } else {
       S.thy[fb][fa] = th;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) S.dy[c][fb][fa] = d[c];
+      for (int c = 0; c < 4; ++c) {
+        S.eoy[c][fb][fa] = Mo[c] - pL[c];
+        S.eiy[c][fb][fa] = Mi[c] - pR[c];
+        S.noy[c][fb][fa] = no[c];
+        S.niy[c][fb][fa] = ni[c];
+      }
     }
-    // streamed populations owned by this face (Eqs. (vlbm1)-(vlbm4))
     if (R_in) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) dst[(4 + kout * 4 + c) * plane + offR] = Mo[c] + th * (Mo[c] - pL[c]);
+      for (int c = 0; c < 4; ++c) dst[(4 + kout * 4 + c) * plane + offR] = no[c];
     }
     if (L_in) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) dst[(4 + kin * 4 + c) * plane + offL] = Mi[c] + th * (Mi[c] - pR[c]);
+      for (int c = 0; c < 4; ++c) dst[(4 + kin * 4 + c) * plane + offL] = ni[c];
     }
   }
   __syncthreads();
@@ -306,14 +326,22 @@ __global__ void __launch_bounds__(NT, 2) step_f64_kernel(const Launch L) {
     const int lx = tid % TX, ly = tid / TX;
     const int gi = i0 + lx, gj = j0 + ly;
     if (gi <= nx - 2 && gj <= ny - 2) {
-      const int gx = lx + 1, gy = ly + 1;
+      // Eq. (vlbm5) as written: the new populations, alpha u, and the four
+      // theta-weighted non-equilibrium terms of the cell itself
+      const double thw = S.thx[ly][lx], the = S.thx[ly][lx + 1], ths = S.thy[ly][lx], thn = S.thy[ly + 1][lx];
       double q[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        double v = S.ulf[c][gy][gx] + S.thx[ly][lx] * S.dx[c][ly][lx];
-        v = v - S.thx[ly][lx + 1] * S.dx[c][ly][lx + 1];
-        v = v + S.thy[ly][lx] * S.dy[c][ly][lx];
-        v = v - S.thy[ly + 1][lx] * S.dy[c][ly + 1][lx];
+        const double n1 = S.nox[c][ly][lx], n2 = S.nix[c][ly][lx + 1];
+        const double n3 = S.noy[c][ly][lx], n4 = S.niy[c][ly + 1][lx];
+        double v = n1 + n2;
+        v = v + n3;
+        v = v + n4;
+        v = v + alpha * S.u[c][ly + 2][lx + 2];
+        v = v - thw * S.eix[c][ly][lx];
+        v = v - the * S.eox[c][ly][lx + 1];
+        v = v - ths * S.eiy[c][ly][lx];
+        v = v - thn * S.eoy[c][ly + 1][lx];
         q[c] = v;
       }
       const size_t off = (size_t)gj * nxp + gi;

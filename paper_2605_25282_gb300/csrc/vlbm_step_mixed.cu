@@ -38,7 +38,7 @@ struct Smem {
   float4 gRy[TY + 1][TX];  //          g'_4(R), R frame
   float thx[TY][TX + 1];
   float thy[TY + 1][TX];
-  unsigned long long lam[NT / 32];
+  unsigned lam[NT / 32];
   int flags[NT / 32];
 };
 
@@ -160,15 +160,15 @@ __global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
   float4* __restrict__ dst = reinterpret_cast<float4*>(D.lat) + ((size_t)(par ^ 1) * L.M + m) * D.real_stride;
 
   Ctx k;
-  k.gamma = (float)L.ph.gamma;
-  k.gm1 = (float)(L.ph.gamma - 1.0);
-  k.rg = (float)(1.0 / (L.ph.gamma - 1.0));
-  k.alpha = (float)L.ph.alpha;
-  k.c1 = (float)((1.0 - L.ph.alpha) / 4.0);
+  k.gamma = L.pf.gamma;
+  k.gm1 = L.pf.gm1;
+  k.rg = L.pf.rg;
+  k.alpha = L.pf.alpha;
+  k.c1 = L.pf.c1;
   k.h = rs->inv2a_f;
-  k.rel = (float)L.ph.rlmp_rel;
-  k.absb = (float)L.ph.rlmp_abs;
-  k.eps = (float)L.ph.eps_pos;
+  k.rel = L.pf.rel;
+  k.absb = L.pf.absb;
+  k.eps = L.pf.eps;
   const float dinv = rs->dinv2a_f;
   const int limiter = L.ph.limiter;
 
@@ -404,11 +404,11 @@ __global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
       }
     }
   }
-  unsigned long long lb = lam_to_bits((double)lam);
+  // lambda >= 0: its FP32 bit pattern orders like an unsigned integer
+  unsigned lb = __float_as_uint(lam);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, lb, o);
-    lb = ob > lb ? ob : lb;
+    lb = max(lb, __shfl_xor_sync(0xffffffffu, lb, o));
     flags |= __shfl_xor_sync(0xffffffffu, flags, o);
   }
   if ((tid & 31) == 0) {
@@ -417,13 +417,14 @@ __global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
   }
   __syncthreads();
   if (tid == 0) {
-    unsigned long long best = 0;
+    unsigned best = 0;
     int fl = 0;
     for (int w = 0; w < NT / 32; ++w) {
-      best = S.lam[w] > best ? S.lam[w] : best;
+      best = max(best, S.lam[w]);
       fl |= S.flags[w];
     }
-    atomicMax(&rs->lam_next_bits, best);
+    // one FP32 -> FP64 conversion per CTA
+    atomicMax(&rs->lam_next_bits, lam_to_bits((double)__uint_as_float(best)));
     if (fl) atomicOr(&rs->flags, fl);
   }
 }

@@ -1,8 +1,16 @@
 """Mixed path (FP32 storage, rest-frame FP32 arithmetic) against the FP64 oracle.
 
-Short horizon, per cell: the FP32 state carries ~6e-8 relative rounding per
-step; over 10 steps and the jet's amplification the bound below is what the
-FP32 arithmetic allows (derivation in the comparison norms' docstring).
+Short horizon, per cell.  Two effects set the bound:
+  - the FP32 positivity floors are raised to 1e-5 of the first-order state
+    (a margin against FP32 rounding); where the pressure constraint binds this
+    moves p by O(1e-5) relative (a float64 emulation of the same rest-frame
+    arithmetic with these floors differs from the oracle by rho 3e-6,
+    p 4e-5 after 10 steps of the 200 x 100 jet);
+  - FP32 rounding of the rest-frame terms: each step adds ~2^-24 of the
+    largest rest-frame energy term, rho |dv|^2 / 2 for the velocity jumps dv
+    between neighbours, to the internal energy.  Next to the jet, where the
+    ambient gas sits beside a moving stream, that is a few 1e-4 of p.
+Hence rho and v within 1e-4 (v relative to |v1| + |v2| + c) and p within 2e-3.
 """
 
 import numpy as np
@@ -13,7 +21,8 @@ from tests import gpu_helpers as H
 
 pytestmark = pytest.mark.gpu
 
-RTOL32 = 2e-4
+RTOL_RHO_V = 1e-4
+RTOL_P = 2e-3
 
 
 def mixed_errors(nx, ny, M, n, limiter=2):
@@ -39,7 +48,7 @@ def mixed_errors(nx, ny, M, n, limiter=2):
 def test_mixed_jet_10_steps(limiter):
     e = mixed_errors(200, 100, 4, 10, limiter)
     print("mixed vs FP64 oracle after 10 steps:", e)
-    assert e["rho"] <= RTOL32 and e["p"] <= RTOL32 and e["v"] <= RTOL32, e
+    assert e["rho"] <= RTOL_RHO_V and e["v"] <= RTOL_RHO_V and e["p"] <= RTOL_P, e
     assert e["t"] <= 1e-6
 
 
@@ -53,8 +62,8 @@ def test_mixed_ragged_multilevel():
         g = O.Grid(nx, ny)
         for m in range(2):
             rho, v1, v2, p = O.moments(g, H.oracle_params(), ref["u"][m])
-            assert (np.abs(mo["rho"][m] - rho) / rho).max() <= RTOL32
-            assert (np.abs(mo["p"][m] - p) / p).max() <= RTOL32
+            assert (np.abs(mo["rho"][m] - rho) / rho).max() <= RTOL_RHO_V
+            assert (np.abs(mo["p"][m] - p) / p).max() <= RTOL_P
 
 
 def test_mixed_positivity_over_smallest_config():
