@@ -186,6 +186,34 @@ int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const v
                       int b_is_f32, int nxb, int nyb, int M, double* mean_a, double* std_a,
                       double* mean_b, double* std_b, double* w1, void* cuda_stream);
 
+/* Sec. 3.3-3.4, Eqs. (mean), (std), (w1disc), (strongError): the error
+ * functionals between ensemble a [M][nya][nxa] and ensemble b [M][nyb][nxb]
+ * (b block-restricted onto a's grid as in stats_w1_mean_std), written to the
+ * device array out[4] = {E_mean, E_std, W_11, E_strong}: cell averages of
+ * |mean_a - mean_b|, |std_a - std_b| and of the one-point W1, and the
+ * realization average of ||a_m - R b_m||_1 / ||R b_m||_1.  Every sum runs in a
+ * fixed order (the result is reproducible bit for bit).  Scratch memory
+ * (3 * 512 + 128 M doubles) comes from the stream-ordered allocator
+ * (cudaMallocAsync) and is released on the stream.  1 <= M <= 4096.  Asynchronous. */
+int stats_error_functionals(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32,
+                            int nxb, int nyb, int M, double* out, void* cuda_stream);
+
+/* Sec. 4.3, Eq. (empcdf): per-cell empirical quantiles
+ * p_alpha = inf{xi : F(xi) >= alpha} (the ceil(alpha M)-th smallest sample) of
+ * ensemble [M][ny][nx] (device; FP32 when is_f32 != 0) for the probabilities
+ * probs[0..nprob-1] (host array, each in (0, 1], nprob <= 16); out is a device
+ * array [nprob][ny][nx] (FP64).  1 <= M <= 4096.  Asynchronous. */
+int stats_quantiles(const void* ens, int is_f32, int nx, int ny, int M, const double* probs, int nprob, double* out,
+                    void* cuda_stream);
+
+/* Sec. 4.4, Eq. (hist): per-cell histogram density of ensemble [M][ny][nx]
+ * on the bins [edges[j], edges[j+1]), j = 0..nbins-1 (edges: device array of
+ * nbins + 1 increasing values), out[j][y][x] = count / (M (edges[j+1] -
+ * edges[j])); samples outside [edges[0], edges[nbins]) are not counted.
+ * nbins <= 8192.  Asynchronous. */
+int stats_histogram(const void* ens, int is_f32, int nx, int ny, int M, const double* edges, int nbins, double* out,
+                    void* cuda_stream);
+
 /* Checkpoint of the whole context state (every level and realization, times,
  * step counts, kinetic-speed bookkeeping) to host memory.  With host_buf NULL,
  * *bytes receives the size needed.  Synchronises the stream.  Restoring with

@@ -96,10 +96,11 @@ class Grid:
     ny: int
     x_max: float = 2.5
     y_min: float | None = None  # default: centred, y in [-ny dx / 2, ny dx / 2]
+    cell: float | None = None  # explicit cell size (a sub-domain of a larger grid)
 
     @property
     def dx(self) -> float:
-        return self.x_max / self.nx
+        return self.x_max / self.nx if self.cell is None else self.cell
 
     @property
     def y0(self) -> float:
@@ -308,3 +309,68 @@ def stats_w1_mean_std(ens_a: np.ndarray, ens_b: np.ndarray):
         raise ValueError("fine grid must be an integer refinement of the coarse grid")
     b = restrict(ens_b, r) if r > 1 else np.asarray(ens_b, dtype=np.float64)
     return ensemble_stats(ens_a, b)
+
+
+# --------------------------------------------------------------------------- #
+# Error functionals and diagnostics (Sec. 3.3-3.4, Sec. 4.3).                  #
+# --------------------------------------------------------------------------- #
+
+
+def error_functionals(ens_a: np.ndarray, ens_b: np.ndarray):
+    """(E_mean, E_std, W_11, E_strong) between a coarse ensemble [M, ny, nx]
+    and a fine one [M, r ny, r nx] restricted onto it (Eqs. mean, std,
+    w1disc, strongError): cell averages of |mean_a - mean_b|, |std_a - std_b|
+    and of the one-point W1, and the realization average of the relative L1
+    distance ||a_m - R b_m||_1 / ||R b_m||_1 (the L1 norms as sums over the
+    common grid: the cell size cancels)."""
+    ens_a = np.asarray(ens_a, dtype=np.float64)
+    r = ens_b.shape[-1] // ens_a.shape[-1]
+    b = restrict(ens_b, r) if r > 1 else np.asarray(ens_b, dtype=np.float64)
+    mean_a, std_a, mean_b, std_b, w1 = ensemble_stats(ens_a, b)
+    n = mean_a.size
+    e_mean = np.abs(mean_a - mean_b).sum() / n
+    e_std = np.abs(std_a - std_b).sum() / n
+    w11 = w1.sum() / n
+    M = ens_a.shape[0]
+    strong = 0.0
+    for m in range(M):
+        strong += np.abs(ens_a[m] - b[m]).sum() / np.abs(b[m]).sum()
+    return e_mean, e_std, w11, strong / M
+
+
+def quantile(samples: np.ndarray, alpha: float) -> np.ndarray:
+    """Empirical alpha-quantile per cell, Eq. (empcdf):
+    p_alpha = inf{xi : F(xi) >= alpha} = the ceil(alpha M)-th smallest sample."""
+    s = np.sort(np.asarray(samples, dtype=np.float64), axis=0)
+    M = s.shape[0]
+    k = int(np.ceil(alpha * M))
+    k = min(max(k, 1), M)
+    return s[k - 1]
+
+
+def width_ratio(samples: np.ndarray) -> np.ndarray:
+    """Quantile width ratio Q = (p95 - p5) / (p84 - p16), Eq. (widthratio)."""
+    return (quantile(samples, 0.95) - quantile(samples, 0.05)) / (quantile(samples, 0.84) - quantile(samples, 0.16))
+
+
+def histogram(samples: np.ndarray, edges: np.ndarray) -> np.ndarray:
+    """Per-cell histogram density on bins [edges[j], edges[j+1]), Eq. (hist):
+    f = count / (M |B_j|); samples outside [edges[0], edges[-1]) are not
+    counted.  samples [M, ...cells] -> [nbins, ...cells]."""
+    s = np.asarray(samples, dtype=np.float64)
+    M = s.shape[0]
+    nb = len(edges) - 1
+    out = np.zeros((nb,) + s.shape[1:])
+    for j in range(nb):
+        inside = (s >= edges[j]) & (s < edges[j + 1])
+        out[j] = inside.sum(axis=0) / (M * (edges[j + 1] - edges[j]))
+    return out
+
+
+def rate_fit(dx, err):
+    """Least-squares slope and intercept of log(err) against log(dx), Eq. (ratefit)."""
+    x = np.log(np.asarray(dx, dtype=np.float64))
+    y = np.log(np.asarray(err, dtype=np.float64))
+    A = np.stack([x, np.ones_like(x)], axis=1)
+    (r, c), *_ = np.linalg.lstsq(A, y, rcond=None)
+    return float(r), float(c)

@@ -19,10 +19,13 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvlbm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["vlbm_api.cu", "vlbm_aux.cu", "vlbm_stats.cu", "vlbm_step_f64.cu", "vlbm_step_mixed.cu"]
-# The FP64 path evaluates every expression in the oracle's order with separate
-# roundings (no FMA contraction), so it agrees with the oracle to round-off.
-PER_FILE = {"vlbm_step_f64.cu": ["-fmad=false"], "vlbm_aux.cu": ["-fmad=false"]}
+SOURCES = ["vlbm_api.cu", "vlbm_aux.cu", "vlbm_diag.cu", "vlbm_stats.cu", "vlbm_step_f64.cu", "vlbm_step_mixed.cu"]
+# No implicit FMA contraction: the FP64 path evaluates every expression in the
+# oracle's order with separate roundings, so it agrees with the oracle to
+# round-off; the mixed path spells out each fused multiply-add, so every tile
+# shape and launch design computes bit-identical results.
+PER_FILE = {"vlbm_step_f64.cu": ["-fmad=false"], "vlbm_aux.cu": ["-fmad=false"],
+            "vlbm_step_mixed.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE]
 

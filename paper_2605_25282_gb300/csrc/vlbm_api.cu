@@ -9,6 +9,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <new>
@@ -18,11 +19,17 @@
 #include "vlbm_internal.cuh"
 
 namespace vlbm {
+size_t functional_scratch_doubles(int M);
+int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why);
+cudaError_t functional_launch(const void* a, int a_f32, int nxa, int nya, const void* b, int b_f32, int nxb, int M,
+                              double* scratch, double* out, cudaStream_t s);
+int quantile_launch(const void* ens, int f32, int nx, int ny, int M, const double* probs, int nprob, double* out,
+                    cudaStream_t s, const char** why);
+int histogram_launch(const void* ens, int f32, int nx, int ny, int M, const double* edges, int nbins, double* out,
+                     cudaStream_t s, const char** why);
 int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32, int nxb,
                  int nyb, int M, double* mean_a, double* std_a, double* mean_b, double* std_b, double* w1,
                  cudaStream_t s, const char** why);
-void tiles_f64(int nx, int ny, int* tx, int* ty);
-void tiles_mixed(int nx, int ny, int* tx, int* ty);
 }  // namespace vlbm
 
 using namespace vlbm;
@@ -40,8 +47,9 @@ thread_local bool g_capturing = false;
 struct LevelMem {
   void* lat = nullptr;
   double* inlet = nullptr;
+  float4* inlet_f = nullptr;
   RealState* rs = nullptr;
-  size_t lat_bytes = 0, inlet_bytes = 0, rs_bytes = 0;
+  size_t lat_bytes = 0, inlet_bytes = 0, inlet_f_bytes = 0, rs_bytes = 0;
 };
 
 }  // namespace
@@ -70,6 +78,8 @@ struct vlbm_ctx {
   int* d_count = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool warmed = false;
+  int variant = -1;  // mixed kernel launch design (index), -1: not tuned yet
+  std::vector<float> tune_ms;  // time per step of every variant when tuned
   std::string err = "no error";
 };
 
@@ -108,6 +118,7 @@ void release_levels(vlbm_ctx* c) {
   for (auto& m : c->mem) {
     dev_free(c, m.lat);
     dev_free(c, m.inlet);
+    dev_free(c, m.inlet_f);
     dev_free(c, m.rs);
   }
   c->mem.clear();
@@ -118,9 +129,54 @@ void release_levels(vlbm_ctx* c) {
   c->warmed = false;
 }
 
+// Picks the mixed kernel's launch design (tile shape, one tile per CTA or
+// persistent) by timing every variant on the live state.  A step launch
+// without the tick that follows it is idempotent: it rewrites the same next
+// lattice and max-reduces the same lambda.  The environment variable
+// VLBM_MIXED_VARIANT (an index) forces a variant.
+int tune_mixed(vlbm_ctx* c) {
+  if (c->variant >= 0) return VLBM_OK;
+  if (const char* env = std::getenv("VLBM_MIXED_VARIANT")) {
+    const int v = std::atoi(env);
+    if (v >= 0 && v < mixed_variants()) {
+      c->variant = v;
+      return VLBM_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(c, VLBM_ECUDA, "cudaEventCreate");
+  float best = 1e30f;
+  int best_v = 1;
+  c->tune_ms.assign(mixed_variants(), 0.0f);
+  for (int v = 0; v < mixed_variants(); ++v) {
+    cudaError_t e = launch_step_mixed(c->launch, v, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_step_mixed(c->launch, v, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(c, e, "tuning the mixed kernel");
+    }
+    c->tune_ms[v] = ms / 2;
+    if (ms < best) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->variant = best_v;
+  return VLBM_OK;
+}
+
 int launch_one_step(vlbm_ctx* c) {
   cudaError_t e = c->precision == VLBM_FP64 ? launch_step_f64(c->launch, c->stream)
-                                             : launch_step_mixed(c->launch, c->stream);
+                                             : launch_step_mixed(c->launch, c->variant, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   e = launch_tick(c->launch, c->precision, 1, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "tick kernel launch");
@@ -154,6 +210,10 @@ int build_graph(vlbm_ctx* c) {
 int run_steps(vlbm_ctx* c, long long n) {
   // the first steps run as plain launches (this also configures the kernels'
   // shared-memory limits before any capture)
+  if (n > 0 && c->precision == VLBM_MIXED) {
+    int st = tune_mixed(c);
+    if (st) return st;
+  }
   while (n > 0 && !c->warmed) {
     int st = launch_one_step(c);
     if (st) return st;
@@ -194,7 +254,11 @@ int read_flags(vlbm_ctx* c, int level_only, std::vector<RealState>* out_level) {
     cudaError_t e = cudaMemcpy(h.data(), c->mem[l].rs, sizeof(RealState) * c->M, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "reading realization state");
     for (int m = 0; m < c->M; ++m) {
-      if (h[m].flags & 2) {
+      if (h[m].flags & 4) {
+        worst = VLBM_ETIMEOUT;
+        fail(c, worst, "level " + std::to_string(l) + " realization " + std::to_string(m) +
+                           ": a bounded device wait gave up");
+      } else if ((h[m].flags & 2) && worst != VLBM_ETIMEOUT) {
         worst = VLBM_ENONFINITE;
         fail(c, worst, "level " + std::to_string(l) + " realization " + std::to_string(m) + ": non-finite state");
       } else if ((h[m].flags & 1) && worst == VLBM_OK) {
@@ -331,11 +395,13 @@ int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, con
       LevelMem& mm = c->mem[l];
       mm.lat_bytes = 2 * (size_t)M * real;
       mm.inlet_bytes = (size_t)M * 4 * g.ny * sizeof(double);
+      mm.inlet_f_bytes = (size_t)M * g.ny * sizeof(float4);
       mm.rs_bytes = (size_t)M * sizeof(RealState);
       mm.lat = dev_alloc(c, mm.lat_bytes);
       mm.inlet = static_cast<double*>(dev_alloc(c, mm.inlet_bytes));
+      mm.inlet_f = static_cast<float4*>(dev_alloc(c, mm.inlet_f_bytes));
       mm.rs = static_cast<RealState*>(dev_alloc(c, mm.rs_bytes));
-      if (!mm.lat || !mm.inlet || !mm.rs) {
+      if (!mm.lat || !mm.inlet || !mm.inlet_f || !mm.rs) {
         release_levels(c);
         c->M = 0;
         c->initialized = false;
@@ -375,14 +441,13 @@ int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, con
     D.y_min = g.y_min;
     D.plane = (size_t)g.ny * D.nx_pad;
     D.real_stride = c->precision == VLBM_FP64 ? 20 * D.plane : 5 * D.plane;
-    if (c->precision == VLBM_FP64)
-      tiles_f64(g.nx, g.ny, &D.tiles_x, &D.tiles_y);
-    else
-      tiles_mixed(g.nx, g.ny, &D.tiles_x, &D.tiles_y);
+    // FP64 tiles here; the mixed kernel lays out its own tiles per shape
+    tiles_f64(g.nx, g.ny, &D.tiles_x, &D.tiles_y);
     D.tile_begin = tiles;
     tiles += D.tiles_x * D.tiles_y;
     D.lat = c->mem[l].lat;
     D.inlet = c->mem[l].inlet;
+    D.inlet_f = c->mem[l].inlet_f;
     D.rs = c->mem[l].rs;
   }
   L.total_tiles = tiles;
@@ -511,11 +576,42 @@ int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const v
   return VLBM_OK;
 }
 
+int stats_error_functionals(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32,
+                            int nxb, int nyb, int M, double* out, void* cuda_stream) {
+  const char* why = "";
+  if (!ens_a || !ens_b || !out) return fail(nullptr, VLBM_EINVAL, "ensemble and output pointers must be non-NULL");
+  int st = functional_check(nxa, nya, nxb, nyb, M, &why);
+  if (st) return fail(nullptr, st, why);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  double* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), functional_scratch_doubles(M) * sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMallocAsync for the functional scratch");
+  e = functional_launch(ens_a, a_is_f32, nxa, nya, ens_b, b_is_f32, nxb, M, scratch, out, s);
+  cudaError_t e2 = cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "error functional kernels");
+  if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "cudaFreeAsync");
+  return VLBM_OK;
+}
+
+int stats_quantiles(const void* ens, int is_f32, int nx, int ny, int M, const double* probs, int nprob, double* out,
+                    void* cuda_stream) {
+  const char* why = "";
+  int st = quantile_launch(ens, is_f32, nx, ny, M, probs, nprob, out, static_cast<cudaStream_t>(cuda_stream), &why);
+  return st ? fail(nullptr, st, why) : VLBM_OK;
+}
+
+int stats_histogram(const void* ens, int is_f32, int nx, int ny, int M, const double* edges, int nbins, double* out,
+                    void* cuda_stream) {
+  const char* why = "";
+  int st = histogram_launch(ens, is_f32, nx, ny, M, edges, nbins, out, static_cast<cudaStream_t>(cuda_stream), &why);
+  return st ? fail(nullptr, st, why) : VLBM_OK;
+}
+
 int vlbm_save(vlbm_ctx* c, void* host_buf, size_t* bytes) {
   if (!c || !bytes) return fail(c, VLBM_EINVAL, "ctx and bytes are required");
   if (!c->initialized) return fail(c, VLBM_ESTATE, "nothing to save before vlbm_init_ensemble");
   size_t need = 5 * sizeof(uint32_t) + sizeof(uint8_t) * 8;
-  for (auto& m : c->mem) need += m.rs_bytes + m.inlet_bytes + m.lat_bytes;
+  for (auto& m : c->mem) need += m.rs_bytes + m.inlet_bytes + m.inlet_f_bytes + m.lat_bytes;
   if (!host_buf) {
     *bytes = need;
     return VLBM_OK;
@@ -532,7 +628,7 @@ int vlbm_save(vlbm_ctx* c, void* host_buf, size_t* bytes) {
   p += 8;
   for (auto& m : c->mem) {
     for (auto [src, n] : {std::pair<const void*, size_t>{m.rs, m.rs_bytes}, {m.inlet, m.inlet_bytes},
-                          {m.lat, m.lat_bytes}}) {
+                          {m.inlet_f, m.inlet_f_bytes}, {m.lat, m.lat_bytes}}) {
       e = cudaMemcpy(p, src, n, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint copy");
       p += n;
@@ -546,7 +642,7 @@ int vlbm_load(vlbm_ctx* c, const void* host_buf, size_t bytes) {
   if (!c || !host_buf) return fail(c, VLBM_EINVAL, "ctx and host_buf are required");
   if (!c->initialized) return fail(c, VLBM_ESTATE, "call vlbm_init_ensemble with the same M before vlbm_load");
   size_t need = 5 * sizeof(uint32_t) + 8;
-  for (auto& m : c->mem) need += m.rs_bytes + m.inlet_bytes + m.lat_bytes;
+  for (auto& m : c->mem) need += m.rs_bytes + m.inlet_bytes + m.inlet_f_bytes + m.lat_bytes;
   if (bytes != need) return fail(c, VLBM_EINVAL, "checkpoint size does not match this context");
   const unsigned char* p = static_cast<const unsigned char*>(host_buf);
   uint32_t hdr[5];
@@ -559,7 +655,7 @@ int vlbm_load(vlbm_ctx* c, const void* host_buf, size_t bytes) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
   for (auto& m : c->mem) {
     for (auto [dst, n] : {std::pair<void*, size_t>{m.rs, m.rs_bytes}, {m.inlet, m.inlet_bytes},
-                          {m.lat, m.lat_bytes}}) {
+                          {m.inlet_f, m.inlet_f_bytes}, {m.lat, m.lat_bytes}}) {
       e = cudaMemcpy(dst, p, n, cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint restore");
       p += n;

@@ -92,6 +92,7 @@ __global__ void inlet_kernel(const Launch L, const PerturbDev P) {
   }
   const double p = fabs(y) <= P.r_jet ? L.ph.jet_p : L.ph.amb_p;
   double* inl = D.inlet + (size_t)m * 4 * D.ny;
+  D.inlet_f[(size_t)m * D.ny + j] = make_float4((float)rho, (float)v1, 0.0f, (float)p);
   inl[0 * D.ny + j] = rho;
   inl[1 * D.ny + j] = __dmul_rn(rho, v1);
   inl[2 * D.ny + j] = 0.0;

@@ -17,6 +17,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/vlbm.h"
@@ -41,7 +42,7 @@ struct RealState {
   unsigned long long lam_next_bits;  // lambda(u^{n+1}) accumulated by the running step
   int active;          // the pending step runs for this realization
   int landing;         // the pending step lands on t_target
-  int flags;           // sticky: 1 non-positive, 2 non-finite
+  int flags;           // sticky: 1 non-positive, 2 non-finite, 4 bounded wait gave up
   int gref_set;        // MIXED: inv2a_prev is valid
 };
 
@@ -54,6 +55,7 @@ struct LevelDesc {
   size_t real_stride;    // elements (double or float4) per realization and lattice
   void* lat;             // lattice storage base
   double* inlet;         // [M][4][ny] conserved inlet state (FP64)
+  float4* inlet_f;       // [M][ny] inlet primitives (rho, v1, v2, p) in FP32 (mixed kernel)
   RealState* rs;         // [M]
 };
 
@@ -80,6 +82,11 @@ struct Launch {
   int M;
   int total_tiles;
   LevelDesc lv[kMaxLevels];
+  // TMA descriptors of the mixed kernel, filled per launch for the tile shape
+  // in use: nodal-state boxes (radius-2 halo) and non-equilibrium boxes
+  // (radius-1 halo, all four populations) of each level's lattice storage.
+  CUtensorMap tmP[kMaxLevels];
+  CUtensorMap tmG[kMaxLevels];
 };
 
 // Ordered bits of a non-negative double (monotone as unsigned integers).
@@ -105,9 +112,17 @@ void add_launches(unsigned n);
 
 // Launch helpers implemented in the kernel translation units.
 cudaError_t launch_step_f64(const Launch& L, cudaStream_t s);
-cudaError_t launch_step_mixed(const Launch& L, cudaStream_t s);
 size_t step_f64_smem_bytes();
-size_t step_mixed_smem_bytes();
+void tiles_f64(int nx, int ny, int* tx, int* ty);
+
+// Mixed kernel launch designs 0..mixed_variants()-1: 32 x TY tiles, one tile
+// per CTA or persistent CTAs with double-buffered TMA prefetch.
+int mixed_variants();
+int mixed_variant_rows(int variant);
+bool mixed_variant_persistent(int variant);
+// Fills the tile decomposition and TMA descriptors of `variant` into a copy of
+// L and launches; returns cudaErrorNotSupported if the driver lacks TMA encode.
+cudaError_t launch_step_mixed(const Launch& L, int variant, cudaStream_t s);
 
 cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, cudaStream_t s);
 cudaError_t launch_init_state(const Launch& L, int precision, cudaStream_t s);

@@ -15,68 +15,107 @@
 // so FP32 keeps p to FP32 relative accuracy: no FP64 in the loop (GB300's
 // FP64 rate is 1/58 of FP32).
 //
-// Tile phases as in the FP64 kernel: P1 nodal states (radius-2 halo), P2
-// first-order state U_LF and bounds in each node's frame (radius-1 halo), P3
-// faces (theta_f with the R-theta limiter in both cells' frames), P4 update,
-// new rest-frame non-equilibrium parts, boundaries and lambda.
+// One CTA advances a 32 x TY tile of one realization on one level:
+//   load  one elected thread issues two TMA tensor loads on an mbarrier: the
+//         nodal states of the tile + radius-2 halo, and the four
+//         non-equilibrium planes of the tile + radius-1 halo
+//   P2    first-order state U_LF and relaxed density bounds of every node of
+//         the tile + radius-1 halo, each in its own rest frame; the four
+//         boosted upwind Maxwellians of every tile cell are kept
+//   P3    every face touching the tile: the exact a_{n-1} -> a_n change of its
+//         two non-equilibrium parts, theta_f (R-theta limiter, evaluated in
+//         both cells' frames; a division-free test covers the common case)
+//         and theta_f d_f in both frames
+//   P4    update (Eq. (vlbm5) regrouped per face, in the cell's frame), new
+//         nodal state, new rest-frame non-equilibrium parts (Eqs. (vlbm1)-(vlbm4))
+//         from the kept Maxwellians and theta_f d_f, zero-gradient copies,
+//         inlet column, lambda for a_{n+1}.
+// Every wait on the mbarrier is bounded; a CTA that gives up raises flag 4 on
+// its realization and returns.
+#include <cudaTypedefs.h>
+
 #include "vlbm_internal.cuh"
 
 namespace vlbm {
 namespace {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int HX = TX + 4, HY = TY + 4;
-constexpr int GX = TX + 2, GY = TY + 2;
+constexpr int TX = 32;
+constexpr int kWaitIters = 1 << 22;
 
-struct Smem {
-  float4 P[HY][HX];      // (rho, v1, v2, p) of tile + 2 halo
-  float4 U[GY][GX];      // U_LF in the node's own frame, tile + 1 halo
-  float4 B[GY][GX];      // lo_b, hi_b, eps_rho, eps_p
-  float4 gLx[TY][TX + 1];  // x faces: g'_1(L) (a_n), L frame
-  float4 gRx[TY][TX + 1];  //          g'_2(R) (a_n), R frame
-  float4 gLy[TY + 1][TX];  // y faces: g'_3(L), L frame
-  float4 gRy[TY + 1][TX];  //          g'_4(R), R frame
+template <int TY>
+struct Boxes {
+  static constexpr int HX = TX + 4, HY = TY + 4, GX = TX + 2, GY = TY + 2;
+  alignas(128) float4 P[HY][HX];     // TMA box: (rho, v1, v2, p), tile + 2 halo
+  alignas(128) float4 G[4][GY][GX];  // TMA box: g'_k, tile + 1 halo
+};
+
+template <int TY>
+struct Work {
+  static constexpr int GX = TX + 2, GY = TY + 2;
+  float4 U[GY][GX];                  // U_LF in the node's own frame
+  float2 B[GY][GX];                  // relaxed density bounds lo - delta, hi + delta
+  float4 Mk[4][TY][TX];              // B_vc M_k(u_upwind) of every tile cell (frame of the cell)
+  float4 tdLx[TY][TX + 1], tdRx[TY][TX + 1];  // theta_f d_f in L's / R's frame, x faces
+  float4 tdLy[TY + 1][TX], tdRy[TY + 1][TX];  // same, y faces
   float thx[TY][TX + 1];
   float thy[TY + 1][TX];
-  unsigned lam[NT / 32];
-  int flags[NT / 32];
+  unsigned lam[TX * TY / 32];
+  int flags[TX * TY / 32];
+};
+
+// one tile per CTA
+template <int TY>
+struct SmemTile {
+  Boxes<TY> box;
+  Work<TY> w;
+  alignas(8) unsigned long long bar;
+};
+
+// persistent CTA: tile k and the prefetch of tile k + 1
+template <int TY>
+struct SmemPersist {
+  Boxes<TY> buf[2];
+  Work<TY> w;
+  int issued[2];  // a TMA load is in flight for buf[b]
+  alignas(8) unsigned long long bar[2];
 };
 
 struct Ctx {
-  float gamma, gm1, rg;  // gamma, gamma - 1, 1 / (gamma - 1)
+  float gamma, gm1, rg;
   float alpha, c1;
-  float h;               // 1 / (2 a_n), FP32 (rounded down)
+  float h;
   float rel, absb, eps;
 };
+
+__device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+__device__ __forceinline__ float4 add(float4 a, float4 b) { return f4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ float4 sub(float4 a, float4 b) { return f4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ float4 scale(float s, float4 x) { return f4(s * x.x, s * x.y, s * x.z, s * x.w); }
+__device__ __forceinline__ float4 axpy(float s, float4 x, float4 y) {
+  return f4(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z), fmaf(s, x.w, y.w));
+}
 
 // B_w u of a node with primitive state P; d = velocity relative to w.
 __device__ __forceinline__ float4 boosted(const float4 P, float w1, float w2, const Ctx& k, float& d1, float& d2) {
   d1 = P.y - w1;
   d2 = P.z - w2;
   const float r = P.x;
-  return make_float4(r, r * d1, r * d2, P.w * k.rg + 0.5f * r * (d1 * d1 + d2 * d2));
+  return f4(r, r * d1, r * d2, fmaf(0.5f * r, fmaf(d1, d1, d2 * d2), P.w * k.rg));
 }
 
 // Boosted lab fluxes B_w f(u) = f(u') + w1 u' and B_w g(u) = g(u') + w2 u'.
 __device__ __forceinline__ float4 xflux(const float4 u, float d1, float d2, float p, float w1) {
-  return make_float4(u.y + w1 * u.x, u.y * d1 + p + w1 * u.y, u.y * d2 + w1 * u.z, (u.w + p) * d1 + w1 * u.w);
+  return f4(fmaf(w1, u.x, u.y), fmaf(w1, u.y, fmaf(u.y, d1, p)), fmaf(w1, u.z, u.y * d2), fmaf(w1, u.w, (u.w + p) * d1));
 }
 __device__ __forceinline__ float4 yflux(const float4 u, float d1, float d2, float p, float w2) {
-  return make_float4(u.z + w2 * u.x, u.y * d2 + w2 * u.y, u.z * d2 + p + w2 * u.z, (u.w + p) * d2 + w2 * u.w);
+  return f4(fmaf(w2, u.x, u.z), fmaf(w2, u.y, u.y * d2), fmaf(w2, u.z, fmaf(u.z, d2, p)), fmaf(w2, u.w, (u.w + p) * d2));
 }
 
 // Boost of a rest-frame vector x by dw = w_new - w_old.
 __device__ __forceinline__ float4 boost(const float4 x, float dw1, float dw2) {
-  const float m1 = x.y - dw1 * x.x, m2 = x.z - dw2 * x.x;
-  const float E = x.w - (dw1 * x.y + dw2 * x.z) + 0.5f * (dw1 * dw1 + dw2 * dw2) * x.x;
-  return make_float4(x.x, m1, m2, E);
-}
-
-__device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
-__device__ __forceinline__ float4 add(float4 a, float4 b) { return f4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ __forceinline__ float4 sub(float4 a, float4 b) { return f4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-__device__ __forceinline__ float4 axpy(float s, float4 x, float4 y) {
-  return f4(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z), fmaf(s, x.w, y.w));
+  const float m1 = fmaf(-dw1, x.x, x.y), m2 = fmaf(-dw2, x.x, x.z);
+  const float E = fmaf(0.5f * fmaf(dw1, dw1, dw2 * dw2), x.x, x.w - fmaf(dw1, x.y, dw2 * x.z));
+  return f4(x.x, m1, m2, E);
 }
 
 // d_f = [M_out(u_L) - u_out,L] - [M_in(u_R) - u_in,R] = g_in(R) - g_out(L)
@@ -89,36 +128,43 @@ __device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float
 }
 
 // Largest theta in [0, 1] keeping U0 + theta D admissible and inside the
-// relaxed density bounds; the same convex-set argument as the FP64 rule, in
-// the cell's rest frame (no cancellation in the pressure quadratic).
-__device__ float theta_star(const float4 U0, const float4 D, const float4 Bd, const Ctx& k) {
+// relaxed density bounds [lo_b, hi_b], in the cell's rest frame (no
+// cancellation in the pressure quadratic).  The floors eps_rho, eps_p are
+// min(value, max(eps_pos, 1e-5 value)) of the first-order state U0: the
+// relative margin keeps the final average admissible despite FP32 rounding.
+// theta = 1 is tested first, without any division (the common case).
+__device__ float theta_star(const float4 U0, const float4 D, const float2 Bd, const Ctx& k) {
+  const float er = fminf(U0.x, fmaxf(k.eps, 1e-5f * U0.x));
+  const float lower = fmaxf(er, Bd.x);
+  const float4 V = add(U0, D);
+  const float pLF = k.gm1 * fmaf(-0.5f, __fdividef(fmaf(U0.y, U0.y, U0.z * U0.z), U0.x), U0.w);
+  const float ep = fminf(pLF, fmaxf(k.eps, 1e-5f * pLF));
+  const float kk = ep * k.rg;
+  // q(theta) = rho E - |m|^2 / 2 - kk rho at theta = 1
+  if (V.x >= lower && V.x <= Bd.y && fmaf(V.x, V.w - kk, -0.5f * fmaf(V.y, V.y, V.z * V.z)) >= 0.0f) return 1.0f;
   float th = 1.0f;
-  const float lower = fmaxf(Bd.z, Bd.x);
-  if (D.x < 0.0f) {
-    th = fminf(th, (U0.x - lower) / (-D.x));
-  } else if (D.x > 0.0f) {
-    th = fminf(th, (Bd.y - U0.x) / D.x);
+  if (V.x < lower) {
+    th = __fdividef(U0.x - lower, -D.x);
+  } else if (V.x > Bd.y) {
+    th = __fdividef(Bd.y - U0.x, D.x);
   }
-  th = fmaxf(th, 0.0f);
-  const float kk = Bd.w * k.rg;
-  const float C = U0.x * U0.w - 0.5f * (U0.y * U0.y + U0.z * U0.z) - kk * U0.x;
-  const float Bq = U0.x * D.w + D.x * U0.w - (U0.y * D.y + U0.z * D.z) - kk * D.x;
-  const float A = D.x * D.w - 0.5f * (D.y * D.y + D.z * D.z);
-  const float qth = C + th * (Bq + th * A);
-  if (qth >= 0.0f) return th;
+  th = fminf(fmaxf(th, 0.0f), 1.0f);
+  const float C = fmaf(U0.x, U0.w - kk, -0.5f * fmaf(U0.y, U0.y, U0.z * U0.z));
+  const float Bq = fmaf(U0.x, D.w, fmaf(D.x, U0.w - kk, -fmaf(U0.y, D.y, U0.z * D.z)));
+  const float A = fmaf(D.x, D.w, -0.5f * fmaf(D.y, D.y, D.z * D.z));
+  if (fmaf(th, fmaf(th, A, Bq), C) >= 0.0f) return th;
   if (C <= 0.0f) return 0.0f;
   float r;
   if (A == 0.0f) {
-    r = -C / Bq;
+    r = __fdividef(-C, Bq);
   } else {
-    const float disc = fmaxf(Bq * Bq - 4.0f * A * C, 0.0f);
-    const float sq = sqrtf(disc);
+    const float sq = sqrtf(fmaxf(fmaf(Bq, Bq, -4.0f * A * C), 0.0f));
     const float Q = -0.5f * (Bq + copysignf(sq, Bq));
     if (Q == 0.0f) return 0.0f;
-    const float r1 = Q / A, r2 = C / Q;
+    const float r1q = __fdividef(Q, A), r2q = __fdividef(C, Q);
     r = -1.0f;
-    if (r1 > 0.0f) r = r1;
-    if (r2 > 0.0f && (r < 0.0f || r2 < r)) r = r2;
+    if (r1q > 0.0f) r = r1q;
+    if (r2q > 0.0f && (r < 0.0f || r2q < r)) r = r2q;
     if (r < 0.0f) return 0.0f;
   }
   return fminf(fmaxf(r, 0.0f), th);
@@ -128,37 +174,75 @@ __device__ __forceinline__ bool is_boundary(int i, int j, int nx, int ny) {
   return i == 0 || i == nx - 1 || j == 0 || j == ny - 1;
 }
 
-// non-equilibrium part g'_k(a_n) of an interior node: stored part plus the
-// exact change of its equilibrium from a_prev to a_n, B_v F(u) (1/2a_prev - 1/2a_n)
-// with B_v f(u) = (rho v1, p, 0, v1 rho e) and B_v g(u) = (rho v2, 0, p, v2 rho e).
-__device__ __forceinline__ float4 corrected(float4 g, const float4 P, int k, float dinv, const Ctx& c) {
-  const float re = P.w * c.rg;
-  float4 F = (k < 2) ? f4(P.x * P.y, P.w, 0.0f, P.y * re) : f4(P.x * P.z, 0.0f, P.w, P.z * re);
-  const float s = (k % 2 == 0) ? dinv : -dinv;
-  return axpy(s, F, g);
+// ---- TMA / mbarrier (inline PTX) ------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
 }
 
-__global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
-  const int tid = threadIdx.x;
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-  int tile = blockIdx.x;
-  int lvl = 0;
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for phase `phase` of the barrier for at most one second.
+__device__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t phase) {
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, phase))
+    if (globaltimer() - t0 > 1000000000ull) return false;
+  return true;
+}
+
+// Work unit u -> (level, realization, tile within the level); units run over
+// the tiles of realization 0 first, so CTAs in flight share halos through L2.
+__device__ __forceinline__ void decode_unit(const Launch& L, long long u, int& lvl, int& m, int& tile) {
+  m = (int)(u / L.total_tiles);
+  tile = (int)(u - (long long)m * L.total_tiles);
+  lvl = 0;
   while (lvl + 1 < L.nlevels && tile >= L.lv[lvl + 1].tile_begin) ++lvl;
-  const LevelDesc& D = L.lv[lvl];
-  tile -= D.tile_begin;
-  const int m = blockIdx.y;
-  RealState* rs = D.rs + m;
-  if (!rs->active) return;
+  tile -= L.lv[lvl].tile_begin;
+}
 
+// Computes one tile whose boxes are in Bx (P2, P3, P4 and the lambda
+// reduction); ends with every thread past a barrier after its last use of W.
+template <int TY>
+__device__ __forceinline__ void compute_tile(const Launch& L, Boxes<TY>& Bx, Work<TY>& W, int lvl, int m, int tile) {
+  constexpr int NT = TX * TY, GX = Boxes<TY>::GX, GY = Boxes<TY>::GY;
+  const int tid = threadIdx.x;
+  const LevelDesc& D = L.lv[lvl];
+  RealState* rs = D.rs + m;
   const int nx = D.nx, ny = D.ny, nxp = D.nx_pad;
   const size_t plane = D.plane;
   const int par = (int)(rs->steps & 1);
-  const float4* __restrict__ src =
-      reinterpret_cast<const float4*>(D.lat) + ((size_t)par * L.M + m) * D.real_stride;
   float4* __restrict__ dst = reinterpret_cast<float4*>(D.lat) + ((size_t)(par ^ 1) * L.M + m) * D.real_stride;
-
   Ctx k;
   k.gamma = L.pf.gamma;
   k.gm1 = L.pf.gm1;
@@ -171,19 +255,8 @@ __global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
   k.eps = L.pf.eps;
   const float dinv = rs->dinv2a_f;
   const int limiter = L.ph.limiter;
-
   const int i0 = 1 + (tile % D.tiles_x) * TX;
   const int j0 = 1 + (tile / D.tiles_x) * TY;
-
-  // ---- P1 -------------------------------------------------------------------
-  for (int idx = tid; idx < HX * HY; idx += NT) {
-    const int li = idx % HX, lj = idx / HX;
-    int gi = i0 - 2 + li, gj = j0 - 2 + lj;
-    gi = gi < 0 ? 0 : (gi > nx - 1 ? nx - 1 : gi);
-    gj = gj < 0 ? 0 : (gj > ny - 1 ? ny - 1 : gj);
-    S.P[lj][li] = src[(size_t)gj * nxp + gi];
-  }
-  __syncthreads();
 
   // ---- P2: U_LF in each node's own frame, bounds ----------------------------
   for (int idx = tid; idx < GX * GY; idx += NT) {
@@ -191,99 +264,119 @@ __global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
     const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
     if (gi < 1 || gi > nx - 2 || gj < 1 || gj > ny - 2) continue;
     const int hx = li + 1, hy = lj + 1;
-    const float4 Pc = S.P[hy][hx];
+    const float4 Pc = Bx.P[hy][hx];
     const float w1 = Pc.y, w2 = Pc.z;
     float d1, d2;
-    const float4 PW = S.P[hy][hx - 1], PE = S.P[hy][hx + 1], PS = S.P[hy - 1][hx], PN = S.P[hy + 1][hx];
+    const float4 PW = Bx.P[hy][hx - 1], PE = Bx.P[hy][hx + 1], PS = Bx.P[hy - 1][hx], PN = Bx.P[hy + 1][hx];
     const float4 uW = boosted(PW, w1, w2, k, d1, d2);
-    const float4 FW = xflux(uW, d1, d2, PW.w, w1);
+    const float4 M1 = axpy(k.h, xflux(uW, d1, d2, PW.w, w1), scale(k.c1, uW));
     const float4 uE = boosted(PE, w1, w2, k, d1, d2);
-    const float4 FE = xflux(uE, d1, d2, PE.w, w1);
+    const float4 M2 = axpy(-k.h, xflux(uE, d1, d2, PE.w, w1), scale(k.c1, uE));
     const float4 uS = boosted(PS, w1, w2, k, d1, d2);
-    const float4 GS = yflux(uS, d1, d2, PS.w, w2);
+    const float4 M3 = axpy(k.h, yflux(uS, d1, d2, PS.w, w2), scale(k.c1, uS));
     const float4 uN = boosted(PN, w1, w2, k, d1, d2);
-    const float4 GN = yflux(uN, d1, d2, PN.w, w2);
-    const float4 sumu = add(add(uW, uE), add(uS, uN));
-    const float4 sumF = add(sub(FW, FE), sub(GS, GN));
-    float4 U = axpy(k.h, sumF, f4(k.c1 * sumu.x, k.c1 * sumu.y, k.c1 * sumu.z, k.c1 * sumu.w));
-    if (k.alpha != 0.0f) U = add(U, f4(k.alpha * Pc.x, 0.0f, 0.0f, k.alpha * Pc.w * k.rg));
-    S.U[lj][li] = U;
-    float lo = fminf(fminf(Pc.x, fminf(PW.x, PE.x)), fminf(fminf(PS.x, PN.x), U.x));
-    float hi = fmaxf(fmaxf(Pc.x, fmaxf(PW.x, PE.x)), fmaxf(fmaxf(PS.x, PN.x), U.x));
-    const float delta = k.rel * (hi - lo) + k.absb;
-    const float pLF = k.gm1 * (U.w - 0.5f * (U.y * U.y + U.z * U.z) / U.x);
-    // FP32 floors: a relative margin of 1e-5 keeps the final average
-    // admissible despite FP32 rounding (the FP64 rule uses eps_pos alone).
-    const float er = fminf(U.x, fmaxf(k.eps, 1e-5f * U.x));
-    const float ep = fminf(pLF, fmaxf(k.eps, 1e-5f * pLF));
-    S.B[lj][li] = f4(lo - delta, hi + delta, er, ep);
+    const float4 M4 = axpy(-k.h, yflux(uN, d1, d2, PN.w, w2), scale(k.c1, uN));
+    float4 U = add(add(M1, M2), add(M3, M4));
+    if (k.alpha != 0.0f) U = add(U, f4(k.alpha * Pc.x, 0.0f, 0.0f, (k.alpha * Pc.w) * k.rg));
+    W.U[lj][li] = U;
+    if (li >= 1 && li <= TX && lj >= 1 && lj <= TY) {
+      W.Mk[0][lj - 1][li - 1] = M1;
+      W.Mk[1][lj - 1][li - 1] = M2;
+      W.Mk[2][lj - 1][li - 1] = M3;
+      W.Mk[3][lj - 1][li - 1] = M4;
+    }
+    const float lo = fminf(fminf(Pc.x, fminf(PW.x, PE.x)), fminf(fminf(PS.x, PN.x), U.x));
+    const float hi = fmaxf(fmaxf(Pc.x, fmaxf(PW.x, PE.x)), fmaxf(fmaxf(PS.x, PN.x), U.x));
+    const float delta = fmaf(k.rel, hi - lo, k.absb);
+    W.B[lj][li] = make_float2(lo - delta, hi + delta);
   }
   __syncthreads();
 
   // ---- P3: faces -------------------------------------------------------------
-  constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
-  for (int idx = tid; idx < NXF + NYF; idx += NT) {
-    const bool xdir = idx < NXF;
-    int fa, fb, iL, jL, iR, jR;
-    bool L_in, R_in;
-    if (xdir) {
-      fa = idx % (TX + 1);
-      fb = idx / (TX + 1);
-      iL = i0 + fa - 1;
-      jL = j0 + fb;
-      iR = iL + 1;
-      jR = jL;
-      if (jL > ny - 2) continue;
-      L_in = fa >= 1 && iL <= nx - 2;
-      R_in = fa < TX && iR <= nx - 2;
-    } else {
-      const int q = idx - NXF;
-      fa = q % TX;
-      fb = q / TX;
-      iL = i0 + fa;
-      jL = j0 + fb - 1;
-      iR = iL;
-      jR = jL + 1;
-      if (iL > nx - 2) continue;
-      L_in = fb >= 1 && jL <= ny - 2;
-      R_in = fb < TY && jR <= ny - 2;
-    }
-    if (!L_in && !R_in) continue;
-    const int kout = xdir ? 0 : 2, kin = xdir ? 1 : 3;
-    const bool bL = is_boundary(iL, jL, nx, ny), bR = is_boundary(iR, jR, nx, ny);
-    const float4 PL = S.P[jL - j0 + 2][iL - i0 + 2], PR = S.P[jR - j0 + 2][iR - i0 + 2];
-    const float4 zero = f4(0.f, 0.f, 0.f, 0.f);
-    const float4 gL = bL ? zero : corrected(src[(1 + kout) * plane + (size_t)jL * nxp + iL], PL, kout, dinv, k);
-    const float4 gR = bR ? zero : corrected(src[(1 + kin) * plane + (size_t)jR * nxp + iR], PR, kin, dinv, k);
-    float th;
-    if (bL && bR) {
-      th = 0.0f;
-    } else if (limiter == 0) {
-      th = 0.0f;
-    } else if (limiter == 1) {
-      th = 1.0f;
-    } else {
-      float tL = 1.0f, tR = 1.0f;
-      if (!bL) {
-        const float4 dL = d_in_L(gL, gR, PL, PR);
-        const int gx = iL - i0 + 1, gy = jL - j0 + 1;
-        tL = theta_star(S.U[gy][gx], f4(-4.f * dL.x, -4.f * dL.y, -4.f * dL.z, -4.f * dL.w), S.B[gy][gx], k);
+  // Thread (lx, ly) owns the west and south faces of its cell; the east faces
+  // of the last column and the north faces of the top row go to the first
+  // warps.  A face brings its two non-equilibrium parts to a_n (the exact
+  // change B_v F(u) (1/2a_{n-1} - 1/2a_n) of the equilibrium, with
+  // B_v f(u) = (rho v1, p, 0, v1 rho e), B_v g(u) = (rho v2, 0, p, v2 rho e)),
+  // writes them back (each is used by this face alone), and stores theta_f
+  // and theta_f d_f in both cells' frames.
+  {
+    const int lx = tid % TX, ly = tid / TX;
+    constexpr int NEXTRA = TY + TX;
+    for (int pass = 0; pass < 3; ++pass) {
+      bool xdir;
+      int fa, fb;
+      if (pass < 2) {
+        xdir = pass == 0;
+        fa = lx;
+        fb = ly;
+      } else {
+        if (tid >= NEXTRA) break;
+        xdir = tid < TY;
+        fa = xdir ? TX : tid - TY;
+        fb = xdir ? tid : TY;
       }
-      if (!bR) {
-        const float4 dR = d_in_R(gL, gR, PL, PR);
-        const int gx = iR - i0 + 1, gy = jR - j0 + 1;
-        tR = theta_star(S.U[gy][gx], f4(4.f * dR.x, 4.f * dR.y, 4.f * dR.z, 4.f * dR.w), S.B[gy][gx], k);
+      int iL, jL, iR, jR;
+      bool L_in, R_in;
+      if (xdir) {
+        iL = i0 + fa - 1;
+        jL = j0 + fb;
+        iR = iL + 1;
+        jR = jL;
+        if (jL > ny - 2) continue;
+        L_in = fa >= 1 && iL <= nx - 2;
+        R_in = fa < TX && iR <= nx - 2;
+      } else {
+        iL = i0 + fa;
+        jL = j0 + fb - 1;
+        iR = iL;
+        jR = jL + 1;
+        if (iL > nx - 2) continue;
+        L_in = fb >= 1 && jL <= ny - 2;
+        R_in = fb < TY && jR <= ny - 2;
       }
-      th = fminf(tL, tR);
-    }
-    if (xdir) {
-      S.thx[fb][fa] = th;
-      S.gLx[fb][fa] = gL;
-      S.gRx[fb][fa] = gR;
-    } else {
-      S.thy[fb][fa] = th;
-      S.gLy[fb][fa] = gL;
-      S.gRy[fb][fa] = gR;
+      if (!L_in && !R_in) continue;
+      const bool bL = is_boundary(iL, jL, nx, ny), bR = is_boundary(iR, jR, nx, ny);
+      const int kout = xdir ? 0 : 2, kin = xdir ? 1 : 3;
+      const int gxL = iL - i0 + 1, gyL = jL - j0 + 1, gxR = iR - i0 + 1, gyR = jR - j0 + 1;
+      const float4 PL = Bx.P[gyL + 1][gxL + 1], PR = Bx.P[gyR + 1][gxR + 1];
+      float4 gL = Bx.G[kout][gyL][gxL], gR = Bx.G[kin][gyR][gxR];
+      if (dinv != 0.0f) {
+        if (!bL) {
+          const float re = PL.w * k.rg;
+          gL = axpy(dinv, xdir ? f4(PL.x * PL.y, PL.w, 0.0f, PL.y * re) : f4(PL.x * PL.z, 0.0f, PL.w, PL.z * re), gL);
+          Bx.G[kout][gyL][gxL] = gL;
+        }
+        if (!bR) {
+          const float re = PR.w * k.rg;
+          gR = axpy(-dinv, xdir ? f4(PR.x * PR.y, PR.w, 0.0f, PR.y * re) : f4(PR.x * PR.z, 0.0f, PR.w, PR.z * re), gR);
+          Bx.G[kin][gyR][gxR] = gR;
+        }
+      }
+      float th;
+      float4 dL = f4(0.f, 0.f, 0.f, 0.f), dR = dL;
+      if ((bL && bR) || limiter == 0) {
+        th = 0.0f;
+      } else {
+        dL = d_in_L(gL, gR, PL, PR);
+        dR = d_in_R(gL, gR, PL, PR);
+        if (limiter == 1) {
+          th = 1.0f;
+        } else {
+          const float tL = bL ? 1.0f : theta_star(W.U[gyL][gxL], scale(-4.f, dL), W.B[gyL][gxL], k);
+          const float tR = bR ? 1.0f : theta_star(W.U[gyR][gxR], scale(4.f, dR), W.B[gyR][gxR], k);
+          th = fminf(tL, tR);
+        }
+      }
+      if (xdir) {
+        W.thx[fb][fa] = th;
+        W.tdLx[fb][fa] = scale(th, dL);
+        W.tdRx[fb][fa] = scale(th, dR);
+      } else {
+        W.thy[fb][fa] = th;
+        W.tdLy[fb][fa] = scale(th, dL);
+        W.tdRy[fb][fa] = scale(th, dR);
+      }
     }
   }
   __syncthreads();
@@ -295,111 +388,83 @@ __global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
     const int lx = tid % TX, ly = tid / TX;
     const int gi = i0 + lx, gj = j0 + ly;
     if (gi <= nx - 2 && gj <= ny - 2) {
-      const int hx = lx + 2, hy = ly + 2;
-      const float4 Pc = S.P[hy][hx];
-      const float4 PW = S.P[hy][hx - 1], PE = S.P[hy][hx + 1], PS = S.P[hy - 1][hx], PN = S.P[hy + 1][hx];
-      const float thW = S.thx[ly][lx], thE = S.thx[ly][lx + 1], thS = S.thy[ly][lx], thN = S.thy[ly + 1][lx];
-      const float4 g1W = S.gLx[ly][lx], g2c = S.gRx[ly][lx];
-      const float4 g1c = S.gLx[ly][lx + 1], g2E = S.gRx[ly][lx + 1];
-      const float4 g3S = S.gLy[ly][lx], g4c = S.gRy[ly][lx];
-      const float4 g3c = S.gLy[ly + 1][lx], g4N = S.gRy[ly + 1][lx];
-      float4 U = S.U[ly + 1][lx + 1];
-      U = axpy(thW, d_in_R(g1W, g2c, PW, Pc), U);
-      U = axpy(-thE, d_in_L(g1c, g2E, Pc, PE), U);
-      U = axpy(thS, d_in_R(g3S, g4c, PS, Pc), U);
-      U = axpy(-thN, d_in_L(g3c, g4N, Pc, PN), U);
+      const int cx = lx + 1, cy = ly + 1;
+      const float4 Pc = Bx.P[ly + 2][lx + 2];
+      const float thW = W.thx[ly][lx], thE = W.thx[ly][lx + 1], thS = W.thy[ly][lx], thN = W.thy[ly + 1][lx];
+      const float4 tdRW = W.tdRx[ly][lx], tdLE = W.tdLx[ly][lx + 1];
+      const float4 tdRS = W.tdRy[ly][lx], tdLN = W.tdLy[ly + 1][lx];
+      // Eq. (vlbm5) regrouped per face: U_LF + sum_f s theta_f d_f, cell frame
+      const float4 U = add(sub(add(W.U[cy][cx], tdRW), tdLE), sub(tdRS, tdLN));
       // new nodal state (rest frame of the old velocity -> primitive)
       const float rn = U.x;
-      const float inv = 1.0f / rn;
+      const float inv = __fdividef(1.0f, rn);
       const float dv1 = U.y * inv, dv2 = U.z * inv;
-      const float ren = U.w - 0.5f * (U.y * dv1 + U.z * dv2);
+      const float ren = fmaf(-0.5f, fmaf(U.y, dv1, U.z * dv2), U.w);
       const float pn = k.gm1 * ren;
       const float wn1 = Pc.y + dv1, wn2 = Pc.z + dv2;
       const float4 Pn = f4(rn, wn1, wn2, pn);
       const size_t off = (size_t)gj * nxp + gi;
       dst[off] = Pn;
-      if (!(isfinite(rn) && isfinite(wn1) && isfinite(wn2) && isfinite(pn))) flags |= 2;
       if (!(rn > 0.0f) || !(pn > 0.0f)) flags |= 1;
-      if (!flags) lam = fmaxf(lam, fmaxf(fabsf(wn1), fabsf(wn2)) + sqrtf(k.gamma * pn / rn));
-      // new non-equilibrium parts in the new rest frame (velocity wn):
-      // g_k^{n+1} = M_k(u_X) - M_k(u^{n+1}) - theta_f g_k(X), Eqs. (vlbm1)-(vlbm4)
+      if (!(fabsf(wn1) + fabsf(wn2) + rn + pn < __int_as_float(0x7f800000))) flags |= 2;
+      // lambda, rounded up by 2^-20 so that a_{n+1} >= 2 lambda despite the
+      // approximate reciprocal
+      if (!flags) lam = (fmaxf(fabsf(wn1), fabsf(wn2)) + sqrtf(k.gamma * pn * inv)) * (1.0f + 0x1p-20f);
+      // New non-equilibrium parts, Eqs. (vlbm1)-(vlbm4):
+      // g_k^{n+1} = M_k(u_X) - theta_f g_k(X) - M_k(u^{n+1}), X the upwind node,
+      // formed in the cell's old frame and boosted once to the new one.  In
+      // that frame B g_1(W) = g_2(c) - d_W (the face's d seen by c), and
+      // likewise for the other three faces.
       {
-        const float4 un = f4(rn, 0.0f, 0.0f, ren);
-        float d1, d2;
-        // k = 1, upwind W
-        {
-          const float4 uX = boosted(PW, wn1, wn2, k, d1, d2);
-          const float4 dF = sub(xflux(uX, d1, d2, PW.w, wn1), f4(wn1 * rn, pn, 0.0f, wn1 * ren));
-          const float4 du = sub(uX, un);
-          float4 g = axpy(k.h, dF, f4(k.c1 * du.x, k.c1 * du.y, k.c1 * du.z, k.c1 * du.w));
-          g = axpy(-thW, boost(g1W, wn1 - PW.y, wn2 - PW.z), g);
-          dst[1 * plane + off] = g;
-        }
-        // k = 2, upwind E
-        {
-          const float4 uX = boosted(PE, wn1, wn2, k, d1, d2);
-          const float4 dF = sub(xflux(uX, d1, d2, PE.w, wn1), f4(wn1 * rn, pn, 0.0f, wn1 * ren));
-          const float4 du = sub(uX, un);
-          float4 g = axpy(-k.h, dF, f4(k.c1 * du.x, k.c1 * du.y, k.c1 * du.z, k.c1 * du.w));
-          g = axpy(-thE, boost(g2E, wn1 - PE.y, wn2 - PE.z), g);
-          dst[2 * plane + off] = g;
-        }
-        // k = 3, upwind S
-        {
-          const float4 uX = boosted(PS, wn1, wn2, k, d1, d2);
-          const float4 dG = sub(yflux(uX, d1, d2, PS.w, wn2), f4(wn2 * rn, 0.0f, pn, wn2 * ren));
-          const float4 du = sub(uX, un);
-          float4 g = axpy(k.h, dG, f4(k.c1 * du.x, k.c1 * du.y, k.c1 * du.z, k.c1 * du.w));
-          g = axpy(-thS, boost(g3S, wn1 - PS.y, wn2 - PS.z), g);
-          dst[3 * plane + off] = g;
-        }
-        // k = 4, upwind N
-        {
-          const float4 uX = boosted(PN, wn1, wn2, k, d1, d2);
-          const float4 dG = sub(yflux(uX, d1, d2, PN.w, wn2), f4(wn2 * rn, 0.0f, pn, wn2 * ren));
-          const float4 du = sub(uX, un);
-          float4 g = axpy(-k.h, dG, f4(k.c1 * du.x, k.c1 * du.y, k.c1 * du.z, k.c1 * du.w));
-          g = axpy(-thN, boost(g4N, wn1 - PN.y, wn2 - PN.z), g);
-          dst[4 * plane + off] = g;
-        }
+        const float dw1 = wn1 - Pc.y, dw2 = wn2 - Pc.z;
+        const float4 cU = scale(k.c1, U);
+        const float4 Fx = scale(k.h, xflux(U, dv1, dv2, pn, Pc.y));
+        const float4 Fy = scale(k.h, yflux(U, dv1, dv2, pn, Pc.z));
+        const float4 g1c = Bx.G[0][cy][cx], g2c = Bx.G[1][cy][cx], g3c = Bx.G[2][cy][cx], g4c = Bx.G[3][cy][cx];
+        float4 X;
+        X = add(axpy(-thW, g2c, sub(W.Mk[0][ly][lx], add(cU, Fx))), tdRW);
+        dst[1 * plane + off] = boost(X, dw1, dw2);
+        X = sub(axpy(-thE, g1c, sub(W.Mk[1][ly][lx], sub(cU, Fx))), tdLE);
+        dst[2 * plane + off] = boost(X, dw1, dw2);
+        X = add(axpy(-thS, g4c, sub(W.Mk[2][ly][lx], add(cU, Fy))), tdRS);
+        dst[3 * plane + off] = boost(X, dw1, dw2);
+        X = sub(axpy(-thN, g3c, sub(W.Mk[3][ly][lx], sub(cU, Fy))), tdLN);
+        dst[4 * plane + off] = boost(X, dw1, dw2);
       }
       // zero-gradient copies: nodal state, equilibrium populations (g' = 0)
-      const bool cx = gi == nx - 2, cyl = gj == 1, cyh = gj == ny - 2;
-      if (cx || cyl || cyh) {
+      const bool cxl = gi == nx - 2, cyl = gj == 1, cyh = gj == ny - 2;
+      if (cxl || cyl || cyh) {
         const float4 z = f4(0.f, 0.f, 0.f, 0.f);
         size_t outs[5];
         int no = 0;
-        if (cx) outs[no++] = off + 1;
+        if (cxl) outs[no++] = off + 1;
         if (cyl) {
           outs[no++] = off - nxp;
-          if (cx) outs[no++] = off - nxp + 1;
+          if (cxl) outs[no++] = off - nxp + 1;
         }
         if (cyh) {
           outs[no++] = off + nxp;
-          if (cx) outs[no++] = off + nxp + 1;
+          if (cxl) outs[no++] = off + nxp + 1;
         }
         for (int o = 0; o < no; ++o) {
           dst[outs[o]] = Pn;
           for (int q = 1; q <= 4; ++q) dst[q * plane + outs[o]] = z;
         }
       }
-      // inlet column (Dirichlet datum, equilibrium populations)
+      // inlet column (Dirichlet datum as FP32 primitives, equilibrium populations)
       if (gi == 1) {
-        const double* inl = D.inlet + (size_t)m * 4 * ny;
+        const float4* inl = D.inlet_f + (size_t)m * ny;
         int rows[3] = {gj, -1, -1};
         if (gj == 1) rows[1] = 0;
         if (gj == ny - 2) rows[2] = ny - 1;
         for (int r = 0; r < 3; ++r) {
           const int jj = rows[r];
           if (jj < 0) continue;
-          const double q0 = inl[jj], q1 = inl[ny + jj], q2 = inl[2 * ny + jj], q3 = inl[3 * ny + jj];
-          const double u1 = q1 / q0, u2 = q2 / q0;
-          const double pi = (L.ph.gamma - 1.0) * (q3 - 0.5 * q0 * (u1 * u1 + u2 * u2));
-          const float4 Pi = f4((float)q0, (float)u1, (float)u2, (float)pi);
+          const float4 Pi = inl[jj];
           const size_t oi = (size_t)jj * nxp;
           dst[oi] = Pi;
           for (int q = 1; q <= 4; ++q) dst[q * plane + oi] = f4(0.f, 0.f, 0.f, 0.f);
-          lam = fmaxf(lam, fmaxf(fabsf(Pi.y), fabsf(Pi.z)) + sqrtf(k.gamma * Pi.w / Pi.x));
+          lam = fmaxf(lam, (fmaxf(fabsf(Pi.y), fabsf(Pi.z)) + sqrtf(k.gamma * Pi.w / Pi.x)) * (1.0f + 0x1p-20f));
         }
       }
     }
@@ -412,44 +477,234 @@ __global__ void __launch_bounds__(NT, 4) step_mixed_kernel(const Launch L) {
     flags |= __shfl_xor_sync(0xffffffffu, flags, o);
   }
   if ((tid & 31) == 0) {
-    S.lam[tid >> 5] = lb;
-    S.flags[tid >> 5] = flags;
+    W.lam[tid >> 5] = lb;
+    W.flags[tid >> 5] = flags;
   }
   __syncthreads();
   if (tid == 0) {
     unsigned best = 0;
     int fl = 0;
     for (int w = 0; w < NT / 32; ++w) {
-      best = max(best, S.lam[w]);
-      fl |= S.flags[w];
+      best = max(best, W.lam[w]);
+      fl |= W.flags[w];
     }
-    // one FP32 -> FP64 conversion per CTA
     atomicMax(&rs->lam_next_bits, lam_to_bits((double)__uint_as_float(best)));
     if (fl) atomicOr(&rs->flags, fl);
   }
 }
 
-}  // namespace
+// Thread 0: starts the two TMA loads of tile (lvl, m, tile) into Bx on bar.
+// The proxy fence orders earlier generic-proxy accesses of Bx before the
+// async-proxy overwrite.
+template <int TY>
+__device__ __forceinline__ void issue_tile(Boxes<TY>& Bx, unsigned long long* bar, const Launch& L, int lvl, int m,
+                                           int tile) {
+  const LevelDesc& D = L.lv[lvl];
+  const int par = (int)(D.rs[m].steps & 1);
+  const int i0 = 1 + (tile % D.tiles_x) * TX, j0 = 1 + (tile / D.tiles_x) * TY;
+  constexpr uint32_t bytes = sizeof(float4) * (Boxes<TY>::HX * Boxes<TY>::HY + 4 * Boxes<TY>::GX * Boxes<TY>::GY);
+  fence_proxy_async();
+  mbar_arrive_expect_tx(bar, bytes);
+  const int zP = (par * L.M + m) * 5;
+  tma_load_4d(&Bx.P[0][0], &L.tmP[lvl], 0, i0 - 2, j0 - 2, zP, bar);
+  tma_load_4d(&Bx.G[0][0][0], &L.tmG[lvl], 0, i0 - 1, j0 - 1, zP + 1, bar);
+}
 
-size_t step_mixed_smem_bytes() { return sizeof(Smem); }
+// One tile per CTA: blockIdx.x = tile over all levels, blockIdx.y = realization.
+template <int TY>
+__global__ void __launch_bounds__(TX* TY, 1024 / (TX * TY)) step_mixed_tile_kernel(const __grid_constant__ Launch L) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SmemTile<TY>& S = *reinterpret_cast<SmemTile<TY>*>(smem_raw);
+  const int tid = threadIdx.x;
+  int tile = blockIdx.x, lvl = 0;
+  while (lvl + 1 < L.nlevels && tile >= L.lv[lvl + 1].tile_begin) ++lvl;
+  tile -= L.lv[lvl].tile_begin;
+  const int m = blockIdx.y;
+  RealState* rs = L.lv[lvl].rs + m;
+  if (!rs->active) return;
+  if (tid == 0) {
+    mbar_init(&S.bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) issue_tile<TY>(S.box, &S.bar, L, lvl, m, tile);
+  const bool ok = mbar_wait_bounded(&S.bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      mbar_wait_bounded(&S.bar, 0);
+      atomicOr(&rs->flags, 4);
+    }
+    return;
+  }
+  compute_tile<TY>(L, S.box, S.w, lvl, m, tile);
+}
 
-cudaError_t launch_step_mixed(const Launch& L, cudaStream_t s) {
+// Persistent: CTA b takes units b, b + gridDim.x, ...; while it computes one
+// tile the TMA engine fills the other buffer with the next one.
+template <int TY>
+__global__ void __launch_bounds__(TX* TY, 1) step_mixed_persistent_kernel(const __grid_constant__ Launch L) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SmemPersist<TY>& S = *reinterpret_cast<SmemPersist<TY>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const long long total = (long long)L.M * L.total_tiles;
+  long long u = blockIdx.x;
+  auto issue = [&](int b, long long unit) {
+    int lvl, m, tile;
+    decode_unit(L, unit, lvl, m, tile);
+    if (!L.lv[lvl].rs[m].active) {
+      S.issued[b] = 0;
+      return;
+    }
+    issue_tile<TY>(S.buf[b], &S.bar[b], L, lvl, m, tile);
+    S.issued[b] = 1;
+  };
+  if (tid == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    mbar_fence_init();
+    S.issued[0] = S.issued[1] = 0;
+  }
+  __syncthreads();
+  if (tid == 0 && u < total) issue(0, u);
+  __syncthreads();
+  uint32_t phase[2] = {0u, 0u};
+  for (int it = 0; u < total; ++it, u += gridDim.x) {
+    const int b = it & 1;
+    if (tid == 0 && u + gridDim.x < total) issue(b ^ 1, u + gridDim.x);
+    if (!S.issued[b]) {
+      __syncthreads();
+      continue;
+    }
+    int lvl, m, tile;
+    decode_unit(L, u, lvl, m, tile);
+    const bool ok = mbar_wait_bounded(&S.bar[b], phase[b]);
+    phase[b] ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      // leave only once the copies in flight have landed (bounded again)
+      if (tid == 0) {
+        mbar_wait_bounded(&S.bar[b], phase[b] ^ 1u);
+        if (S.issued[b ^ 1]) mbar_wait_bounded(&S.bar[b ^ 1], phase[b ^ 1]);
+        atomicOr(&L.lv[lvl].rs[m].flags, 4);
+      }
+      return;
+    }
+    compute_tile<TY>(L, S.buf[b], S.w, lvl, m, tile);
+    __syncthreads();
+  }
+}
+
+// Variants: {tile rows, persistent}.
+constexpr int kRows[] = {4, 8, 8};
+constexpr bool kPersistent[] = {false, false, true};
+constexpr int kNumVariants = 3;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 4-D view of one level's storage as FP32: (4 components, x, y, 10 M planes);
+// plane index (lattice * M + m) * 5 + q.  Out-of-range boxes fill with zeros.
+cudaError_t encode_level(CUtensorMap* map, const LevelDesc& D, int M, int box_x, int box_y, int box_planes) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  cuuint64_t dims[4] = {4, (cuuint64_t)D.nx, (cuuint64_t)D.ny, (cuuint64_t)10 * M};
+  cuuint64_t strides[3] = {16, (cuuint64_t)D.nx_pad * 16, (cuuint64_t)D.plane * 16};
+  cuuint32_t box[4] = {4, (cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_planes};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, D.lat, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Tile decomposition and TMA descriptors of a 32 x TY tile shape.
+template <int TY>
+cudaError_t layout(Launch& L) {
+  int tiles = 0;
+  for (int l = 0; l < L.nlevels; ++l) {
+    LevelDesc& D = L.lv[l];
+    D.tiles_x = (D.nx - 2 + TX - 1) / TX;
+    D.tiles_y = (D.ny - 2 + TY - 1) / TY;
+    D.tile_begin = tiles;
+    tiles += D.tiles_x * D.tiles_y;
+    cudaError_t e = encode_level(&L.tmP[l], D, L.M, Boxes<TY>::HX, Boxes<TY>::HY, 1);
+    if (e == cudaSuccess) e = encode_level(&L.tmG[l], D, L.M, Boxes<TY>::GX, Boxes<TY>::GY, 4);
+    if (e != cudaSuccess) return e;
+  }
+  L.total_tiles = tiles;
+  return cudaSuccess;
+}
+
+template <int TY>
+cudaError_t launch_tile(Launch& L, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem));
+    cudaError_t e = cudaFuncSetAttribute(step_mixed_tile_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(SmemTile<TY>));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid(L.total_tiles, L.M);
-  step_mixed_kernel<<<grid, NT, sizeof(Smem), s>>>(L);
+  cudaError_t e = layout<TY>(L);
+  if (e != cudaSuccess) return e;
+  step_mixed_tile_kernel<TY><<<dim3(L.total_tiles, L.M), TX * TY, sizeof(SmemTile<TY>), s>>>(L);
   add_launches(1);
   return cudaGetLastError();
 }
 
-void tiles_mixed(int nx, int ny, int* tx, int* ty) {
-  *tx = (nx - 2 + TX - 1) / TX;
-  *ty = (ny - 2 + TY - 1) / TY;
+template <int TY>
+cudaError_t launch_persistent(Launch& L, cudaStream_t s) {
+  static int grid_ctas = 0;
+  if (!grid_ctas) {
+    const int smem = (int)sizeof(SmemPersist<TY>);
+    cudaError_t e = cudaFuncSetAttribute(step_mixed_persistent_kernel<TY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mixed_persistent_kernel<TY>, TX * TY, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid_ctas = (per_sm > 0 ? per_sm : 1) * sms;
+  }
+  cudaError_t e = layout<TY>(L);
+  if (e != cudaSuccess) return e;
+  const long long units = (long long)L.M * L.total_tiles;
+  const int grid = (int)(units < grid_ctas ? units : grid_ctas);
+  step_mixed_persistent_kernel<TY><<<grid, TX * TY, sizeof(SmemPersist<TY>), s>>>(L);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int mixed_variants() { return kNumVariants; }
+int mixed_variant_rows(int v) { return kRows[v]; }
+bool mixed_variant_persistent(int v) { return kPersistent[v]; }
+
+cudaError_t launch_step_mixed(const Launch& Lin, int variant, cudaStream_t s) {
+  static thread_local Launch L;  // large (TMA descriptors): kept off the stack
+  L = Lin;
+  switch (variant) {
+    case 0:
+      return launch_tile<4>(L, s);
+    case 1:
+      return launch_tile<8>(L, s);
+    default:
+      return launch_persistent<8>(L, s);
+  }
 }
 
 }  // namespace vlbm

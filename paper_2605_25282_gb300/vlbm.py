@@ -30,7 +30,9 @@ EXPORTED = [
     "vlbm_default_relax", "vlbm_default_perturb", "vlbm_create", "vlbm_init_ensemble",
     "vlbm_init_ensemble_block", "vlbm_kernel_launches", "vlbm_step",
     "vlbm_advance_to", "vlbm_moments", "vlbm_density", "vlbm_time", "vlbm_sync", "vlbm_get_state",
-    "vlbm_set_state", "stats_w1_mean_std", "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_destroy",
+    "vlbm_set_state", "stats_w1_mean_std", "stats_error_functionals",
+    "stats_quantiles", "stats_histogram",
+    "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_destroy",
 ]
 
 
@@ -97,6 +99,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "vlbm_get_state": ([p, i, i, i, p, p], i),
         "vlbm_set_state": ([p, i, i, i, p, p], i),
         "stats_w1_mean_std": ([p, i, i, i, p, i, i, i, i, p, p, p, p, p, p], i),
+        "stats_error_functionals": ([p, i, i, i, p, i, i, i, i, p, p], i),
+        "stats_quantiles": ([p, i, i, i, i, p, i, p, p], i),
+        "stats_histogram": ([p, i, i, i, i, p, i, p, p], i),
         "vlbm_save": ([p, p, ctypes.POINTER(ctypes.c_size_t)], i),
         "vlbm_load": ([p, p, ctypes.c_size_t], i),
         "vlbm_last_error": ([p], ctypes.c_char_p),
@@ -341,3 +346,46 @@ def stats_w1_mean_std(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cu
                                  int(ens_b.dtype == torch.float32), nxb, nyb, M, *[_ptr(o) for o in out],
                                  ctypes.c_void_p(s.cuda_stream)))
     return dict(zip(("mean_a", "std_a", "mean_b", "std_b", "w1"), out))
+
+
+def stats_error_functionals(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cuda.Stream | None = None):
+    """(E_mean, E_std, W_11, E_strong) between ensembles [M, ny, nx] and [M, r ny, r nx] (device tensor [4])."""
+    _require_cuda()
+    lib = load_library()
+    ens_a, ens_b = ens_a.contiguous(), ens_b.contiguous()
+    M, nya, nxa = ens_a.shape
+    _, nyb, nxb = ens_b.shape
+    out = torch.empty(4, dtype=torch.float64, device=ens_a.device)
+    s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
+    _check(lib.stats_error_functionals(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
+                                       int(ens_b.dtype == torch.float32), nxb, nyb, M, _ptr(out),
+                                       ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def stats_quantiles(ens: torch.Tensor, probs, stream: torch.cuda.Stream | None = None):
+    """Per-cell empirical quantiles p_alpha of an ensemble [M, ny, nx] -> [len(probs), ny, nx]."""
+    _require_cuda()
+    lib = load_library()
+    ens = ens.contiguous()
+    M, ny, nx = ens.shape
+    pr = np.ascontiguousarray(probs, dtype=np.float64)
+    out = torch.empty((len(pr), ny, nx), dtype=torch.float64, device=ens.device)
+    s = stream if stream is not None else torch.cuda.current_stream(ens.device)
+    _check(lib.stats_quantiles(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M,
+                               pr.ctypes.data_as(ctypes.c_void_p), len(pr), _ptr(out), ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def stats_histogram(ens: torch.Tensor, edges: torch.Tensor, stream: torch.cuda.Stream | None = None):
+    """Per-cell histogram density of an ensemble [M, ny, nx] on the bins of `edges` -> [nbins, ny, nx]."""
+    _require_cuda()
+    lib = load_library()
+    ens = ens.contiguous()
+    M, ny, nx = ens.shape
+    e = edges.to(ens.device, torch.float64).contiguous()
+    out = torch.empty((e.numel() - 1, ny, nx), dtype=torch.float64, device=ens.device)
+    s = stream if stream is not None else torch.cuda.current_stream(ens.device)
+    _check(lib.stats_histogram(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, _ptr(e), e.numel() - 1,
+                               _ptr(out), ctypes.c_void_p(s.cuda_stream)))
+    return out

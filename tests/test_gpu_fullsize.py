@@ -1,0 +1,62 @@
+"""Parity at full configuration sizes, on outputs the oracle can compute.
+
+- The batched ensemble (M = 1000 realizations of 400 x 200 and 800 x 400 in
+  one launch, mixed precision: the configuration bench.py times): sampled
+  realizations against the oracle after 10 steps.
+- The FP64 refinement ladder up to 5060 x 2530: after n steps a node depends
+  only on nodes at most 2n columns away (radius-2 limiter stencil) and on the
+  global kinetic speed, which the inlet column sets (|v| = 800 there; the
+  ambient medium has lambda = 1.2).  A sub-domain of the first W columns run
+  by the oracle is therefore exact on columns [0, W - 2n); the columns beyond
+  2n stay in the quiescent far field, identical across columns.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batched_ensemble_sampled_realizations():
+    levels = [(400, 200), (800, 400)]
+    M, n = 1000, 10
+    ens = H.gpu_jet(levels, M, precision="mixed")
+    ens.step(n)
+    sample = [0, 511, 999]
+    for l, (nx, ny) in enumerate(levels):
+        g = O.Grid(nx, ny)
+        for m in sample:
+            ref = O.run_jet(g, H.oracle_params(), O.Jet(), 0, m, 1, n, want_pops=False)
+            rho, v1, v2, p = O.moments(g, H.oracle_params(), ref["u"][0])
+            mo = {k: H.to_np(v)[0] for k, v in ens.moments(l, m, 1).items()}
+            assert (np.abs(mo["rho"] - rho) / rho).max() <= 1e-4, (l, m)
+            assert (np.abs(mo["p"] - p) / p).max() <= 2e-3, (l, m)
+        t, s = ens.time(l)
+        assert np.all(s == n)
+    # every realization stayed admissible and distinct realizations differ
+    ens.sync()
+    d = ens.density(1, 0, 2)
+    assert not bool((d[0] == d[1]).all())
+
+
+@pytest.mark.parametrize("nx,ny", [(400, 200), (1600, 800), (5060, 2530)])
+def test_fp64_ladder_level_sampled_columns(nx, ny):
+    n, W = 10, 64
+    ens = H.gpu_jet([(nx, ny)], 1)
+    ens.step(n)
+    u = H.to_np(ens.get_state(0, pops=False)[0])[0]
+    # oracle on the first W columns with the same cell size and rows
+    dx = 2.5 / nx
+    g = O.Grid(W, ny, y_min=-0.5 * ny * dx, cell=dx)
+    ref = O.run_jet(g, H.oracle_params(), O.Jet(), 0, 0, 1, n, want_pops=False)["u"][0]
+    exact = W - 2 * n - 2
+    err = H.rel_err_cons(u[None, :, :, :exact], ref[None, :, :, :exact]).max()
+    assert err <= 1e-12, err
+    # the far field: every column between 2n + 2 and the outlet's reach is the same
+    far = u[:, :, 2 * n + 2: nx - 2 * n - 2]
+    assert np.array_equal(far, np.broadcast_to(far[:, :, :1], far.shape))
+    fr = H.rel_err_cons(far[None, :, :, :1], ref[None, :, :, 2 * n + 2: 2 * n + 3]).max()
+    assert fr <= 1e-12, fr
