@@ -198,6 +198,23 @@ int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const v
 int stats_error_functionals(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32,
                             int nxb, int nyb, int M, double* out, void* cuda_stream);
 
+/* stats_error_functionals without any device allocation.  Some callers
+ * cannot allocate device memory once they are running: a host that hands the
+ * whole GPU to its own pool allocator and forbids other allocations, or a
+ * real-time loop where an allocation's latency or failure is not acceptable.
+ * This call takes its scratch from a fixed device array compiled into the
+ * library (4.2 MB on every GPU that loads it, held until the process exits)
+ * and never calls cudaMalloc, cudaFree or any allocating routine; the caller
+ * still passes the ensembles and the output array.  M must be <= 4096
+ * (VLBM_EINVAL beyond).  The first call on a device looks up the array's
+ * device address (make it before any stream capture on that device).  All
+ * calls share the array: calls that overlap on the GPU race; consecutive
+ * calls do not interfere (each overwrites every partial sum it reads).
+ * Results are identical to stats_error_functionals.  The paper has no
+ * counterpart: it is an interface for such callers.  Asynchronous. */
+int stats_error_functionals_noalloc(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b,
+                                    int b_is_f32, int nxb, int nyb, int M, double* out, void* cuda_stream);
+
 /* Sec. 4.3, Eq. (empcdf): per-cell empirical quantiles
  * p_alpha = inf{xi : F(xi) >= alpha} (the ceil(alpha M)-th smallest sample) of
  * ensemble [M][ny][nx] (device; FP32 when is_f32 != 0) for the probabilities

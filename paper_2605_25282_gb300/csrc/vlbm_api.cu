@@ -20,6 +20,8 @@
 
 namespace vlbm {
 size_t functional_scratch_doubles(int M);
+int noalloc_max_m();
+cudaError_t noalloc_scratch(double** out);
 int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why);
 cudaError_t functional_launch(const void* a, int a_f32, int nxa, int nya, const void* b, int b_f32, int nxb, int M,
                               double* scratch, double* out, cudaStream_t s);
@@ -591,6 +593,24 @@ int stats_error_functionals(const void* ens_a, int a_is_f32, int nxa, int nya, c
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "error functional kernels");
   if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "cudaFreeAsync");
   return VLBM_OK;
+}
+
+int stats_error_functionals_noalloc(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b,
+                                    int b_is_f32, int nxb, int nyb, int M, double* out, void* cuda_stream) {
+  const char* why = "";
+  if (!ens_a || !ens_b || !out) return fail(nullptr, VLBM_EINVAL, "ensemble and output pointers must be non-NULL");
+  if (M > noalloc_max_m())
+    return fail(nullptr, VLBM_EINVAL,
+                "M = " + std::to_string(M) + " exceeds the " + std::to_string(noalloc_max_m()) +
+                    " realizations the allocation-free scratch holds; use stats_error_functionals");
+  int st = functional_check(nxa, nya, nxb, nyb, M, &why);
+  if (st) return fail(nullptr, st, why);
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the functional scratch");
+  e = functional_launch(ens_a, a_is_f32, nxa, nya, ens_b, b_is_f32, nxb, M, scratch, out,
+                        static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? VLBM_OK : cuda_fail(nullptr, e, "error functional kernels");
 }
 
 int stats_quantiles(const void* ens, int is_f32, int nx, int ny, int M, const double* probs, int nprob, double* out,

@@ -14,6 +14,7 @@
 //    E_strong = (1/M) sum_m ||a_m - R b_m||_1 / ||R b_m||_1 (Eq. strongError).
 // Every sum runs in a fixed order, so the result does not depend on scheduling.
 #include <cmath>
+#include <mutex>
 
 #include "vlbm_internal.cuh"
 
@@ -224,6 +225,38 @@ int pow2_at_least(int M) {
 
 size_t functional_scratch_doubles(int M) { return (size_t)3 * kFuncCtas + (size_t)2 * kStrongChunks * M; }
 
+// ---- allocation-free variant -------------------------------------------------
+// Scratch of stats_error_functionals_noalloc: a file-scope device array that
+// every GPU loading the library holds until the process exits (4.2 MB, enough
+// for M <= kNoAllocMaxM).  Every call overwrites all the partial sums it later
+// reads, so nothing carries over from the previous call; calls that overlap on
+// the GPU share the array and race.
+constexpr int kNoAllocMaxM = 4096;
+constexpr size_t kNoAllocDoubles = (size_t)3 * kFuncCtas + (size_t)2 * kStrongChunks * kNoAllocMaxM;
+static __device__ __align__(256) double g_functional_scratch[kNoAllocDoubles];
+
+int noalloc_max_m() { return kNoAllocMaxM; }
+
+// Device address of the scratch array for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+cudaError_t noalloc_scratch(double** out) {
+  static std::mutex mu;
+  static double* cached[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cached[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_functional_scratch);
+    if (e != cudaSuccess) return e;
+    cached[dev] = static_cast<double*>(p);
+  }
+  *out = cached[dev];
+  return cudaSuccess;
+}
 
 int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why) {
   if (nxa < 1 || nya < 1 || M < 1 || M > 4096) {

@@ -30,7 +30,7 @@ EXPORTED = [
     "vlbm_default_relax", "vlbm_default_perturb", "vlbm_create", "vlbm_init_ensemble",
     "vlbm_init_ensemble_block", "vlbm_kernel_launches", "vlbm_step",
     "vlbm_advance_to", "vlbm_moments", "vlbm_density", "vlbm_time", "vlbm_sync", "vlbm_get_state",
-    "vlbm_set_state", "stats_w1_mean_std", "stats_error_functionals",
+    "vlbm_set_state", "stats_w1_mean_std", "stats_error_functionals", "stats_error_functionals_noalloc",
     "stats_quantiles", "stats_histogram",
     "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_destroy",
 ]
@@ -100,6 +100,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "vlbm_set_state": ([p, i, i, i, p, p], i),
         "stats_w1_mean_std": ([p, i, i, i, p, i, i, i, i, p, p, p, p, p, p], i),
         "stats_error_functionals": ([p, i, i, i, p, i, i, i, i, p, p], i),
+        "stats_error_functionals_noalloc": ([p, i, i, i, p, i, i, i, i, p, p], i),
         "stats_quantiles": ([p, i, i, i, i, p, i, p, p], i),
         "stats_histogram": ([p, i, i, i, i, p, i, p, p], i),
         "vlbm_save": ([p, p, ctypes.POINTER(ctypes.c_size_t)], i),
@@ -360,6 +361,25 @@ def stats_error_functionals(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: to
     _check(lib.stats_error_functionals(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
                                        int(ens_b.dtype == torch.float32), nxb, nyb, M, _ptr(out),
                                        ctypes.c_void_p(s.cuda_stream)))
+    return out
+
+
+def stats_error_functionals_noalloc(ens_a: torch.Tensor, ens_b: torch.Tensor, out: torch.Tensor,
+                                    stream: torch.cuda.Stream | None = None):
+    """stats_error_functionals writing into a caller-owned device tensor out[4], with no
+    device allocation by the library (scratch in a fixed device array, M <= 4096)."""
+    _require_cuda()
+    lib = load_library()
+    if not (ens_a.is_contiguous() and ens_b.is_contiguous() and out.is_contiguous()):
+        raise ValueError("ensembles and out must be contiguous device tensors")
+    if out.dtype != torch.float64 or out.numel() < 4:
+        raise ValueError("out must be a float64 device tensor with 4 elements")
+    M, nya, nxa = ens_a.shape
+    _, nyb, nxb = ens_b.shape
+    s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
+    _check(lib.stats_error_functionals_noalloc(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya,
+                                               _ptr(ens_b), int(ens_b.dtype == torch.float32), nxb, nyb, M,
+                                               _ptr(out), ctypes.c_void_p(s.cuda_stream)))
     return out
 
 
