@@ -37,8 +37,13 @@ SEED = 0
 METRIC = "ensemble cell-updates/s (GLUPS) & % HBM roofline, mixed vs FP64, at stated stat error"
 BYTES_PER_UPDATE = {"mixed": 160, "fp64": 320}
 # DRAM traffic of one step-kernel launch from an ncu capture, with the sha256
-# of the kernel source it was taken on (null once the kernel changes).
-NCU_TRAFFIC = {}
+# of the kernel source and the launch design it was taken on (reported as null
+# once either differs).  Mixed: 609.7 MB read + written for the 4.0 M
+# cell-updates of the M = 10 capture, scaled to 400 M cell-updates.
+NCU_TRAFFIC = {
+    "mixed": {"sha": "f7f285993d5443a8", "design": "march30x5w", "bytes_per_launch": 60.97e9,
+              "capture": "M=10, 400x200 + 800x400, scaled by cell-updates"},
+}
 
 
 def peaks():
@@ -187,12 +192,20 @@ def run_ours(args):
     dens_a = torch.empty((M, nya, nxa), dtype=torch.float32, device=dev)
     dens_b = torch.empty((M, nyb, nxb), dtype=torch.float32, device=dev)
     host_out = [torch.empty((nya, nxa), dtype=torch.float64, pin_memory=True) for _ in range(5)]
+    # end-to-end inputs: the KL coefficients of every realization (Sec. 2.3,
+    # Eq. (karhunenExp)), uniform on (-1, 1), in pinned host memory
+    K = vlbm.PerturbParams().K
+    rng = np.random.default_rng(SEED + rank)
+    host_xi = [torch.from_numpy(rng.uniform(-1.0, 1.0, (M, 2 * K))).pin_memory() for _ in range(2)]
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     step_ms = []
 
-    def bench_step(e2e: bool, timed: bool):
-        ens.init(SEED, M, m_begin=m_begin)
+    def bench_step(e2e: bool, timed: bool, it: int = 0):
+        if e2e:
+            ens.init_samples(host_xi[it % 2])
+        else:
+            ens.init(SEED, M, m_begin=m_begin)
         if timed:
             ev[0].record(stream)
         ens.step(S)
@@ -204,6 +217,7 @@ def run_ours(args):
         if e2e:
             for h, k in zip(host_out, ("mean_a", "std_a", "mean_b", "std_b", "w1")):
                 h.copy_(st[k], non_blocking=True)
+            stream.synchronize()  # the caller reads the statistics of this step
         return st
 
     def barrier():
@@ -212,21 +226,23 @@ def run_ours(args):
             dist.barrier()
 
     def timed_loop(e2e: bool):
-        for _ in range(args.warmup):
-            bench_step(e2e, False)
+        for w in range(args.warmup):
+            bench_step(e2e, False, w)
         barrier()
         launches0 = vlbm.kernel_launches()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        h0 = time.perf_counter()
         t0.record(stream)
-        for _ in range(args.steps):
-            bench_step(e2e, not e2e)
+        for it in range(args.steps):
+            bench_step(e2e, not e2e, it)
             if not e2e:
                 torch.cuda.synchronize()
                 step_ms.append(ev[0].elapsed_time(ev[1]))
         t1.record(stream)
         barrier()
-        ms = t0.elapsed_time(t1)
+        # device time for the kernel-only figure; host wall time end to end
+        ms = t0.elapsed_time(t1) if not e2e else (time.perf_counter() - h0) * 1e3
         launches = vlbm.kernel_launches() - launches0
         if dist is not None:
             tt = torch.tensor([ms], device=dev)
@@ -239,6 +255,7 @@ def run_ours(args):
     ms, launches = timed_loop(False)
     clk = clocks.stop()
     ms_e2e, _ = timed_loop(True)
+    design = ens.step_design()
 
     # the FP64 path on the same levels, fewer realizations (rate per cell update)
     fp64 = None
@@ -260,6 +277,26 @@ def run_ours(args):
                 "hbm_frac": r64 * 1e9 * BYTES_PER_UPDATE["fp64"] / (hbm * 1e9)}
         e64.close()
 
+    # error of every statistic of the mixed path against the FP64 path (whose
+    # update is the oracle's arithmetic), same seed and realizations
+    stat_err = None
+    if args.stat_m > 0 and prec == "mixed":
+        stat_err = {"M": args.stat_m, "solver_steps": S, "reference": "FP64 path, same realizations",
+                    "norm": "sum over cells |s_mixed - s_fp64| / sum |s_fp64| (W1: / sum |mean_fp64|)"}
+        ens_m = vlbm.Ensemble(levels, precision="mixed", stream=stream)
+        ens_d = vlbm.Ensemble(levels, precision="fp64", stream=stream)
+        for e in (ens_m, ens_d):
+            e.init(SEED, args.stat_m, m_begin=m_begin)
+            e.step(S)
+        for l, name in enumerate(("coarse", "fine")):
+            st = vlbm.stats_w1_mean_std(ens_m.density(l, f32=False), ens_d.density(l, f32=False), stream=stream)
+            ma, sa, mb, sb, w1 = (st[k].double() for k in ("mean_a", "std_a", "mean_b", "std_b", "w1"))
+            stat_err[name] = {"mean": float((ma - mb).abs().sum() / mb.abs().sum()),
+                              "std": float((sa - sb).abs().sum() / sb.abs().sum()),
+                              "w1": float(w1.sum() / mb.abs().sum())}
+        ens_m.close()
+        ens_d.close()
+
     total_cells = cells_per_solver_step * S * args.steps * world
     value = total_cells / (ms / 1e3) / 1e9
     e2e_value = total_cells / (ms_e2e / 1e3) / 1e9
@@ -268,7 +305,7 @@ def run_ours(args):
     achieved = BYTES_PER_UPDATE[prec] * cells_per_solver_step / kern_s / 1e9
     sha = kernel_sha(prec)
     tr = NCU_TRAFFIC.get(prec)
-    traffic = tr["bytes_per_launch"] if tr and tr["sha"] == sha else None
+    traffic = tr["bytes_per_launch"] if tr and tr["sha"] == sha and tr["design"] == design[1] else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -291,18 +328,20 @@ def run_ours(args):
                              f"{2 * cells_per_solver_step * BYTES_PER_UPDATE[prec] / 2 / 1e9:.0f} GB)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": f"step_{prec}_kernel", "peak_source": f"{src} hbm_gbs",
+                         "kernel": f"step_{prec}_kernel", "design": design[1], "peak_source": f"{src} hbm_gbs",
                          "bytes_per_cell_update": BYTES_PER_UPDATE[prec],
                          "note": "kernel time = CUDA-event time of the S-step graph / S (includes the "
                                  "per-step tick kernel)"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": M * 2 * K * 8,
                     "d2h_bytes_per_step": 5 * nxa * nya * 8,
-                    "note": "public API with the statistics read back to pinned host memory every step; the "
-                            "ensemble inputs are defined by the seed and drawn on the device"},
+                    "note": "host wall clock through the public API: every step copies the KL coefficients "
+                            "of all realizations from pinned host memory (vlbm_init_ensemble_samples), "
+                            "advances, and reads the statistics back to pinned host memory"},
             "gpu_launches": launches,
             "clocks": clk,
             "fp64_path": fp64,
+            "stat_error": stat_err,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
         }
         print(json.dumps(line), flush=True)
@@ -322,6 +361,7 @@ def main():
     ap.add_argument("--solver-steps", type=int, default=64)
     ap.add_argument("--fp64-m", type=int, default=50)
     ap.add_argument("--fp64-steps", type=int, default=8)
+    ap.add_argument("--stat-m", type=int, default=16)
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -113,8 +113,8 @@ void vlbm_default_perturb(vlbm_perturb* perturb);
 /* Sec. 2.1-2.2: validates the problem (grids, gamma > 1, states with
  * rho, p > 0) and creates a context.  Several levels (e.g. the refinement
  * ladder of Sec. 3.3) advance together in every call.  cuda_stream may be
- * NULL: the context then creates and owns a non-blocking stream.  alloc/free
- * may be NULL (cudaMalloc/cudaFree).
+ * NULL: the context then creates and owns a non-blocking stream (at the
+ * first initialising call).  alloc/free may be NULL (cudaMalloc/cudaFree).
  * No device work is done here.  On success *out owns the context. */
 int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_prim* jet,
                 const vlbm_prim* ambient, const vlbm_relax* relax, int precision, void* cuda_stream,
@@ -132,6 +132,19 @@ int vlbm_init_ensemble(vlbm_ctx* ctx, uint64_t seed, int M, const vlbm_perturb* 
  * m alone), so that independent processes can each own a block of one ensemble.
  * Local index r of the context holds global realization m_begin + r. */
 int vlbm_init_ensemble_block(vlbm_ctx* ctx, uint64_t seed, int m_begin, int M, const vlbm_perturb* perturb);
+
+/* As vlbm_init_ensemble, with the random coefficients of Eq. (karhunenExp)
+ * given instead of drawn: realization r = 0..M-1 uses Y_k = xi[r*2K + k - 1]
+ * and Z_k = xi[r*2K + K + k - 1], k = 1..K (K = perturb->K), each the paper's
+ * U(-1, 1) draw (any values in [-1, 1]: quasi-random points, stratified
+ * samples, another code's draws).  Layout: M x 2K doubles, row-major.  xi may
+ * be host or device memory.  Host values are checked to lie in [-1, 1]
+ * (VLBM_EINVAL otherwise); device values are not checked.  The M*2K doubles
+ * are copied on the context's stream: pageable host memory before the call
+ * returns, pinned or device memory asynchronously (keep it valid until the
+ * stream has passed the call).  The coefficients equal to a seed's Philox
+ * draws reproduce vlbm_init_ensemble with that seed bit for bit. */
+int vlbm_init_ensemble_samples(vlbm_ctx* ctx, const double* xi, int M, const vlbm_perturb* perturb);
 
 /* Sec. 2.1, Eqs. (vlbm1)-(vlbm5), with a_n re-evaluated every step
  * (Sec. 2.3): advances every realization on every level by n steps. */
@@ -246,6 +259,17 @@ const char* vlbm_last_error(const vlbm_ctx* ctx);
 /* Number of kernel launches this library has enqueued in this process so far
  * (graph replays count every kernel node).  Instrumentation for benchmarks. */
 unsigned long long vlbm_kernel_launches(void);
+
+/* The launch design the mixed-precision step kernel runs with in ctx: its
+ * index, its name (static storage) and the number of designs.  The designs
+ * (tile shapes, persistent CTAs, warps marching up column strips) compute
+ * bit-identical results; the context picks the fastest by timing each on its
+ * first step, unless the environment variable VLBM_MIXED_VARIANT holds a valid
+ * index.  *index is -1 (and *name "none") for an FP64 context or before the
+ * first step.  Any output pointer may be NULL.  No counterpart in the paper,
+ * whose update has a single implementation.  Returns VLBM_EINVAL for a NULL
+ * ctx. */
+int vlbm_step_design(const vlbm_ctx* ctx, int* index, const char** name, int* count);
 
 /* Frees the context and everything it allocated.  Accepts NULL. */
 void vlbm_destroy(vlbm_ctx* ctx);

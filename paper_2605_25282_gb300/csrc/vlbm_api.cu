@@ -78,6 +78,8 @@ struct vlbm_ctx {
   std::vector<LevelMem> mem;
   Launch launch{};
   int* d_count = nullptr;
+  double* d_xi = nullptr;  // given KL uniforms (vlbm_init_ensemble_samples)
+  size_t xi_bytes = 0;
   cudaGraphExec_t graph = nullptr;
   bool warmed = false;
   int variant = -1;  // mixed kernel launch design (index), -1: not tuned yet
@@ -284,100 +286,29 @@ int check_level(vlbm_ctx* c, int level, int m0, int count) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-void vlbm_default_relax(vlbm_relax* r) {
-  if (!r) return;
-  r->alpha = 0.0;
-  r->kappa = 1.0;
-  r->limiter = VLBM_LIMITER_RTHETA;
-  r->rlmp_rel = 0.1;
-  r->rlmp_abs = 0.0;
-  r->eps_pos = 1e-13;
-}
-
-void vlbm_default_perturb(vlbm_perturb* p) {
-  if (!p) return;
-  std::memset(p, 0, sizeof(*p));
-  p->r_jet = 0.05;
-  p->A = 0.1;
-  p->p_decay = 2.0;
-  p->K = 10;
-  p->use_amp = 0;
-}
-
-int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_prim* jet,
-                const vlbm_prim* ambient, const vlbm_relax* relax, int precision, void* cuda_stream,
-                vlbm_alloc_fn alloc, vlbm_free_fn free_fn, void* alloc_user, vlbm_ctx** out) {
-  if (!out) return fail(nullptr, VLBM_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!levels || nlevels < 1 || nlevels > kMaxLevels)
-    return fail(nullptr, VLBM_EINVAL, "need 1..8 grid levels");
-  if (!jet || !ambient) return fail(nullptr, VLBM_EINVAL, "jet and ambient states are required");
-  if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, VLBM_EINVAL, "gamma must be > 1");
-  if (!(jet->rho > 0) || !(jet->p > 0) || !(ambient->rho > 0) || !(ambient->p > 0))
-    return fail(nullptr, VLBM_EINVAL, "jet and ambient states need rho > 0 and p > 0");
-  if (precision != VLBM_FP64 && precision != VLBM_MIXED) return fail(nullptr, VLBM_EINVAL, "unknown precision");
-  if ((alloc == nullptr) != (free_fn == nullptr))
-    return fail(nullptr, VLBM_EINVAL, "alloc and free callbacks must be given together");
-  vlbm_relax R;
-  vlbm_default_relax(&R);
-  if (relax) R = *relax;
-  if (!(R.alpha >= 0.0 && R.alpha < 1.0)) return fail(nullptr, VLBM_EINVAL, "alpha must be in [0, 1)");
-  if (!(R.kappa >= 1.0)) return fail(nullptr, VLBM_EINVAL, "kappa must be >= 1 (Bouchut bound)");
-  if (R.limiter < 0 || R.limiter > 2) return fail(nullptr, VLBM_EINVAL, "unknown limiter");
-  if (!(R.rlmp_rel >= 0.0) || !(R.rlmp_abs >= 0.0) || !(R.eps_pos >= 0.0))
-    return fail(nullptr, VLBM_EINVAL, "rlmp_rel, rlmp_abs and eps_pos must be >= 0");
-  for (int l = 0; l < nlevels; ++l) {
-    const vlbm_grid& g = levels[l];
-    if (g.nx < 3 || g.ny < 3) return fail(nullptr, VLBM_EINVAL, "every level needs nx, ny >= 3");
-    if ((long long)g.nx * g.ny > (1LL << 31)) return fail(nullptr, VLBM_EINVAL, "level too large");
-    if (!(g.x_max > 0) || !(g.y_max > g.y_min)) return fail(nullptr, VLBM_EINVAL, "empty domain");
-    const double dx = g.x_max / g.nx, dy = (g.y_max - g.y_min) / g.ny;
-    if (std::fabs(dx - dy) > 1e-12 * dx) return fail(nullptr, VLBM_EINVAL, "cells must be square");
+// Returns true when p is device (or managed) memory; host memory otherwise,
+// including when no device is present.
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
-  vlbm_ctx* c = new (std::nothrow) vlbm_ctx();
-  if (!c) return fail(nullptr, VLBM_ENOMEM, "host allocation failed");
-  c->grids.assign(levels, levels + nlevels);
-  c->ph.gamma = gamma;
-  c->ph.alpha = R.alpha;
-  c->ph.kappa = R.kappa;
-  c->ph.limiter = R.limiter;
-  c->ph.rlmp_rel = R.rlmp_rel;
-  c->ph.rlmp_abs = R.rlmp_abs;
-  c->ph.eps_pos = R.eps_pos;
-  c->ph.jet_rho = jet->rho;
-  c->ph.jet_u = jet->u;
-  c->ph.jet_v = jet->v;
-  c->ph.jet_p = jet->p;
-  c->ph.amb_rho = ambient->rho;
-  c->ph.amb_u = ambient->u;
-  c->ph.amb_v = ambient->v;
-  c->ph.amb_p = ambient->p;
-  c->precision = precision;
-  c->alloc = alloc;
-  c->free_fn = free_fn;
-  c->user = alloc_user;
-  if (cuda_stream) {
-    c->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+
+int init_impl(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb* perturb, const double* xi) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  if (c->own_stream && !c->stream) {
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
-      delete c;
-      return cuda_fail(nullptr, e, "cudaStreamCreate");
+      c->stream = nullptr;
+      return cuda_fail(c, e, "cudaStreamCreate");
     }
-    c->own_stream = true;
   }
-  *out = c;
-  return VLBM_OK;
-}
-
-int vlbm_init_ensemble(vlbm_ctx* c, uint64_t seed, int M, const vlbm_perturb* perturb) {
-  return vlbm_init_ensemble_block(c, seed, 0, M, perturb);
-}
-
-int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb* perturb) {
-  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
   if (M < 1 || M > 65535) return fail(c, VLBM_EINVAL, "M must be in [1, 65535]");
   if (m_begin < 0 || (long long)m_begin + M > 0xffffffffLL)
     return fail(c, VLBM_EINVAL, "realization block must lie in [0, 2^32)");
@@ -463,7 +394,22 @@ int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, con
     add_launches(1);
     if (e != cudaSuccess) return cuda_fail(c, e, "clearing the lattice");
   }
-  e = launch_inlet(L, seed, m_begin, P, c->stream);
+  const double* d_xi = nullptr;
+  if (xi) {
+    const size_t bytes = (size_t)M * 2 * P.K * sizeof(double);
+    if (bytes > c->xi_bytes) {
+      dev_free(c, c->d_xi);
+      c->d_xi = static_cast<double*>(dev_alloc(c, bytes));
+      c->xi_bytes = c->d_xi ? bytes : 0;
+      if (!c->d_xi) return fail(c, VLBM_ENOMEM, "device allocation of the KL uniforms failed");
+    }
+    if (bytes) {
+      e = cudaMemcpyAsync(c->d_xi, xi, bytes, cudaMemcpyDefault, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "copying the KL uniforms");
+    }
+    d_xi = c->d_xi;
+  }
+  e = launch_inlet(L, seed, m_begin, P, d_xi, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "inlet kernel");
   e = launch_init_state(L, c->precision, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "initial state kernel");
@@ -479,6 +425,120 @@ int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, con
   c->prepared = false;
   return VLBM_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+void vlbm_default_relax(vlbm_relax* r) {
+  if (!r) return;
+  r->alpha = 0.0;
+  r->kappa = 1.0;
+  r->limiter = VLBM_LIMITER_RTHETA;
+  r->rlmp_rel = 0.1;
+  r->rlmp_abs = 0.0;
+  r->eps_pos = 1e-13;
+}
+
+void vlbm_default_perturb(vlbm_perturb* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->r_jet = 0.05;
+  p->A = 0.1;
+  p->p_decay = 2.0;
+  p->K = 10;
+  p->use_amp = 0;
+}
+
+int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_prim* jet,
+                const vlbm_prim* ambient, const vlbm_relax* relax, int precision, void* cuda_stream,
+                vlbm_alloc_fn alloc, vlbm_free_fn free_fn, void* alloc_user, vlbm_ctx** out) {
+  if (!out) return fail(nullptr, VLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!levels || nlevels < 1 || nlevels > kMaxLevels)
+    return fail(nullptr, VLBM_EINVAL, "need 1..8 grid levels");
+  if (!jet || !ambient) return fail(nullptr, VLBM_EINVAL, "jet and ambient states are required");
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, VLBM_EINVAL, "gamma must be > 1");
+  if (!(jet->rho > 0) || !(jet->p > 0) || !(ambient->rho > 0) || !(ambient->p > 0))
+    return fail(nullptr, VLBM_EINVAL, "jet and ambient states need rho > 0 and p > 0");
+  for (const vlbm_prim* s : {jet, ambient})
+    if (!std::isfinite(s->rho) || !std::isfinite(s->u) || !std::isfinite(s->v) || !std::isfinite(s->p))
+      return fail(nullptr, VLBM_EINVAL, "jet and ambient states must be finite");
+  if (precision != VLBM_FP64 && precision != VLBM_MIXED) return fail(nullptr, VLBM_EINVAL, "unknown precision");
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, VLBM_EINVAL, "alloc and free callbacks must be given together");
+  vlbm_relax R;
+  vlbm_default_relax(&R);
+  if (relax) R = *relax;
+  if (!(R.alpha >= 0.0 && R.alpha < 1.0)) return fail(nullptr, VLBM_EINVAL, "alpha must be in [0, 1)");
+  if (!(R.kappa >= 1.0)) return fail(nullptr, VLBM_EINVAL, "kappa must be >= 1 (Bouchut bound)");
+  if (R.limiter < 0 || R.limiter > 2) return fail(nullptr, VLBM_EINVAL, "unknown limiter");
+  if (!(R.rlmp_rel >= 0.0) || !(R.rlmp_abs >= 0.0) || !(R.eps_pos >= 0.0))
+    return fail(nullptr, VLBM_EINVAL, "rlmp_rel, rlmp_abs and eps_pos must be >= 0");
+  for (int l = 0; l < nlevels; ++l) {
+    const vlbm_grid& g = levels[l];
+    if (g.nx < 3 || g.ny < 3) return fail(nullptr, VLBM_EINVAL, "every level needs nx, ny >= 3");
+    if ((long long)g.nx * g.ny > (1LL << 31)) return fail(nullptr, VLBM_EINVAL, "level too large");
+    if (!(g.x_max > 0) || !(g.y_max > g.y_min)) return fail(nullptr, VLBM_EINVAL, "empty domain");
+    const double dx = g.x_max / g.nx, dy = (g.y_max - g.y_min) / g.ny;
+    if (std::fabs(dx - dy) > 1e-12 * dx) return fail(nullptr, VLBM_EINVAL, "cells must be square");
+  }
+  vlbm_ctx* c = new (std::nothrow) vlbm_ctx();
+  if (!c) return fail(nullptr, VLBM_ENOMEM, "host allocation failed");
+  c->grids.assign(levels, levels + nlevels);
+  c->ph.gamma = gamma;
+  c->ph.alpha = R.alpha;
+  c->ph.kappa = R.kappa;
+  c->ph.limiter = R.limiter;
+  c->ph.rlmp_rel = R.rlmp_rel;
+  c->ph.rlmp_abs = R.rlmp_abs;
+  c->ph.eps_pos = R.eps_pos;
+  c->ph.jet_rho = jet->rho;
+  c->ph.jet_u = jet->u;
+  c->ph.jet_v = jet->v;
+  c->ph.jet_p = jet->p;
+  c->ph.amb_rho = ambient->rho;
+  c->ph.amb_u = ambient->u;
+  c->ph.amb_v = ambient->v;
+  c->ph.amb_p = ambient->p;
+  c->precision = precision;
+  c->alloc = alloc;
+  c->free_fn = free_fn;
+  c->user = alloc_user;
+  // a private stream (cuda_stream NULL) is created by the first call that
+  // enqueues work, so that creating a context touches no device
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->own_stream = cuda_stream == nullptr;
+  *out = c;
+  return VLBM_OK;
+}
+
+int vlbm_init_ensemble(vlbm_ctx* c, uint64_t seed, int M, const vlbm_perturb* perturb) {
+  return vlbm_init_ensemble_block(c, seed, 0, M, perturb);
+}
+
+
+int vlbm_init_ensemble_samples(vlbm_ctx* c, const double* xi, int M, const vlbm_perturb* perturb) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  if (!xi) return fail(c, VLBM_EINVAL, "xi is NULL");
+  if (M < 1 || M > 65535) return fail(c, VLBM_EINVAL, "M must be in [1, 65535]");
+  vlbm_perturb P;
+  vlbm_default_perturb(&P);
+  if (perturb) P = *perturb;
+  if (P.K < 0 || P.K > kMaxModes) return fail(c, VLBM_EINVAL, "K must be in [0, 16]");
+  if (!is_device_pointer(xi)) {
+    const size_t n = (size_t)M * 2 * P.K;
+    for (size_t i = 0; i < n; ++i)
+      if (!(xi[i] >= -1.0 && xi[i] <= 1.0))
+        return fail(c, VLBM_EINVAL, "xi[" + std::to_string(i) + "] is not in [-1, 1]");
+  }
+  return init_impl(c, 0, 0, M, &P, xi);
+}
+
+int vlbm_init_ensemble_block(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb* perturb) {
+  return init_impl(c, seed, m_begin, M, perturb, nullptr);
+}
+
 
 int vlbm_step(vlbm_ctx* c, int n) {
   if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
@@ -687,6 +747,15 @@ int vlbm_load(vlbm_ctx* c, const void* host_buf, size_t bytes) {
 
 unsigned long long vlbm_kernel_launches(void) { return g_launches.load(); }
 
+int vlbm_step_design(const vlbm_ctx* c, int* index, const char** name, int* count) {
+  if (!c) return VLBM_EINVAL;
+  const int v = c->precision == VLBM_MIXED ? c->variant : -1;
+  if (index) *index = v;
+  if (name) *name = v >= 0 ? mixed_variant_name(v) : "none";
+  if (count) *count = mixed_variants();
+  return VLBM_OK;
+}
+
 const char* vlbm_last_error(const vlbm_ctx* c) { return c ? c->err.c_str() : g_thread_error.c_str(); }
 
 void vlbm_destroy(vlbm_ctx* c) {
@@ -694,7 +763,8 @@ void vlbm_destroy(vlbm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   release_levels(c);
   dev_free(c, c->d_count);
-  if (c->own_stream) cudaStreamDestroy(c->stream);
+  dev_free(c, c->d_xi);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 

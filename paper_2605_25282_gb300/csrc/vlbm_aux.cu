@@ -48,6 +48,7 @@ struct PerturbDev {
   int m_begin;
   double amp[kMaxModes];
   uint32_t key0, key1;
+  const double* xi;  // [M][2K] given uniforms (Y then Z), or NULL: Philox draws
 };
 
 // One thread per (level, realization, row).
@@ -59,7 +60,13 @@ __global__ void inlet_kernel(const Launch L, const PerturbDev P) {
   if (j >= D.ny) return;
   // coefficients of realization m (the same for every row; recomputed per thread)
   double Y[kMaxModes], Z[kMaxModes];
-  for (int w = 0; w < 2 * P.K; w += 4) {
+  if (P.xi) {
+    for (int k = 0; k < P.K; ++k) {
+      Y[k] = P.xi[(size_t)m * 2 * P.K + k];
+      Z[k] = P.xi[(size_t)m * 2 * P.K + P.K + k];
+    }
+  }
+  for (int w = 0; !P.xi && w < 2 * P.K; w += 4) {
     uint32_t o[4];
     philox4x32_10((uint32_t)(P.m_begin + m), (uint32_t)(w / 4), 0u, 0u, P.key0, P.key1, o);
     for (int l = 0; l < 4 && w + l < 2 * P.K; ++l) {
@@ -136,8 +143,13 @@ __global__ void init_state_kernel(const Launch L, int precision) {
     for (int c = 0; c < 4; ++c) s[c * D.plane + off] = q[c];
   } else {
     float4* s = reinterpret_cast<float4*>(D.lat) + (size_t)m * D.real_stride;
-    double v1, v2, p;
-    cons_to_prim(q, gamma, v1, v2, p);
+    double v1 = 0.0, v2 = 0.0, p;
+    if (i == 0) {
+      cons_to_prim(q, gamma, v1, v2, p);
+    } else {
+      // the ambient state at rest: cons_to_prim reduces exactly to this
+      p = (gamma - 1.0) * q[3];
+    }
     s[off] = make_float4((float)q[0], (float)v1, (float)v2, (float)p);
     for (int k = 0; k < 4; ++k) s[(1 + k) * D.plane + off] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -507,8 +519,10 @@ inline dim3 node_grid(const LevelDesc& D, int count) {
 
 }  // namespace
 
-cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, cudaStream_t s) {
+cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, const double* xi,
+                         cudaStream_t s) {
   PerturbDev pd{};
+  pd.xi = xi;
   pd.r_jet = P.r_jet;
   pd.K = P.K;
   pd.m_begin = m_begin;

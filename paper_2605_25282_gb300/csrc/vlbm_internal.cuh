@@ -50,6 +50,7 @@ struct LevelDesc {
   int nx, ny, nx_pad;
   int tiles_x, tiles_y;
   int tile_begin;        // first flattened tile index of this level in a step launch
+  int wrows;             // rows per warp (warp-marching step kernel)
   double dx, y_min;
   size_t plane;          // elements per plane (ny * nx_pad)
   size_t real_stride;    // elements (double or float4) per realization and lattice
@@ -115,16 +116,18 @@ cudaError_t launch_step_f64(const Launch& L, cudaStream_t s);
 size_t step_f64_smem_bytes();
 void tiles_f64(int nx, int ny, int* tx, int* ty);
 
-// Mixed kernel launch designs 0..mixed_variants()-1: 32 x TY tiles, one tile
-// per CTA or persistent CTAs with double-buffered TMA prefetch.
+// Mixed kernel launch designs 0..mixed_variants()-1: 32 x TY tiles (one tile
+// per CTA, or persistent CTAs with double-buffered TMA prefetch) and warps
+// marching up column strips.  All compute bit-identical results.
 int mixed_variants();
-int mixed_variant_rows(int variant);
-bool mixed_variant_persistent(int variant);
+const char* mixed_variant_name(int variant);
 // Fills the tile decomposition and TMA descriptors of `variant` into a copy of
 // L and launches; returns cudaErrorNotSupported if the driver lacks TMA encode.
 cudaError_t launch_step_mixed(const Launch& L, int variant, cudaStream_t s);
 
-cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, cudaStream_t s);
+// xi: NULL (Philox draws from seed, m_begin) or device [M][2K] given uniforms.
+cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, const double* xi,
+                         cudaStream_t s);
 cudaError_t launch_init_state(const Launch& L, int precision, cudaStream_t s);
 cudaError_t launch_lambda(const Launch& L, int precision, int level, int m0, int count, cudaStream_t s);
 cudaError_t launch_fill_equilibrium_f64(const Launch& L, int level, int m0, int count, cudaStream_t s);

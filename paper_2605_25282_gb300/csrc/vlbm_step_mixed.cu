@@ -40,7 +40,6 @@ namespace vlbm {
 namespace {
 
 constexpr int TX = 32;
-constexpr int kWaitIters = 1 << 22;
 
 template <int TY>
 struct Boxes {
@@ -132,14 +131,15 @@ __device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float
 // cancellation in the pressure quadratic).  The floors eps_rho, eps_p are
 // min(value, max(eps_pos, 1e-5 value)) of the first-order state U0: the
 // relative margin keeps the final average admissible despite FP32 rounding.
-// theta = 1 is tested first, without any division (the common case).
-__device__ float theta_star(const float4 U0, const float4 D, const float2 Bd, const Ctx& k) {
-  const float er = fminf(U0.x, fmaxf(k.eps, 1e-5f * U0.x));
+// theta = 1 is tested first, without any division (the common case).  The
+// constants come by value so that no context struct lives in local memory.
+__device__ float theta_star(const float4 U0, const float4 D, const float2 Bd, float eps, float gm1, float rg) {
+  const float er = fminf(U0.x, fmaxf(eps, 1e-5f * U0.x));
   const float lower = fmaxf(er, Bd.x);
   const float4 V = add(U0, D);
-  const float pLF = k.gm1 * fmaf(-0.5f, __fdividef(fmaf(U0.y, U0.y, U0.z * U0.z), U0.x), U0.w);
-  const float ep = fminf(pLF, fmaxf(k.eps, 1e-5f * pLF));
-  const float kk = ep * k.rg;
+  const float pLF = gm1 * fmaf(-0.5f, __fdividef(fmaf(U0.y, U0.y, U0.z * U0.z), U0.x), U0.w);
+  const float ep = fminf(pLF, fmaxf(eps, 1e-5f * pLF));
+  const float kk = ep * rg;
   // q(theta) = rho E - |m|^2 / 2 - kk rho at theta = 1
   if (V.x >= lower && V.x <= Bd.y && fmaf(V.x, V.w - kk, -0.5f * fmaf(V.y, V.y, V.z * V.z)) >= 0.0f) return 1.0f;
   float th = 1.0f;
@@ -221,6 +221,177 @@ __device__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t phase) {
   return true;
 }
 
+// ---- per-node and per-face arithmetic shared by every launch design --------
+// Each design calls these with the same operands, so all of them produce
+// bit-identical results (the translation unit is compiled without FMA
+// contraction; every fused multiply-add is an explicit fmaf).
+
+// P2 of an interior node c: U_LF (Eq. (vlbm5)'s first-order part) and the
+// relaxed density bounds, in c's own frame, and the four boosted upwind
+// Maxwellians B_vc M_k(u_upwind) (Eqs. (maxwellians12), (maxwellians34)).
+__device__ __forceinline__ void node_p2(const float4 Pc, const float4 PW, const float4 PE, const float4 PS,
+                                        const float4 PN, const Ctx& k, float4& U, float2& B, float4& M1, float4& M2,
+                                        float4& M3, float4& M4) {
+  const float w1 = Pc.y, w2 = Pc.z;
+  float d1, d2;
+  const float4 uW = boosted(PW, w1, w2, k, d1, d2);
+  M1 = axpy(k.h, xflux(uW, d1, d2, PW.w, w1), scale(k.c1, uW));
+  const float4 uE = boosted(PE, w1, w2, k, d1, d2);
+  M2 = axpy(-k.h, xflux(uE, d1, d2, PE.w, w1), scale(k.c1, uE));
+  const float4 uS = boosted(PS, w1, w2, k, d1, d2);
+  M3 = axpy(k.h, yflux(uS, d1, d2, PS.w, w2), scale(k.c1, uS));
+  const float4 uN = boosted(PN, w1, w2, k, d1, d2);
+  M4 = axpy(-k.h, yflux(uN, d1, d2, PN.w, w2), scale(k.c1, uN));
+  U = add(add(M1, M2), add(M3, M4));
+  if (k.alpha != 0.0f) U = add(U, f4(k.alpha * Pc.x, 0.0f, 0.0f, (k.alpha * Pc.w) * k.rg));
+  const float lo = fminf(fminf(Pc.x, fminf(PW.x, PE.x)), fminf(fminf(PS.x, PN.x), U.x));
+  const float hi = fmaxf(fmaxf(Pc.x, fmaxf(PW.x, PE.x)), fmaxf(fmaxf(PS.x, PN.x), U.x));
+  const float delta = fmaf(k.rel, hi - lo, k.absb);
+  B = make_float2(lo - delta, hi + delta);
+}
+
+// The exact a_{n-1} -> a_n change of a rest-frame non-equilibrium part:
+// g += s (1/2a_{n-1} - 1/2a_n) B_v f(u) with B_v f(u) = (rho v1, p, 0, v1 rho e)
+// (x populations) or B_v g(u) = (rho v2, 0, p, v2 rho e) (y populations);
+// s = +1 for the outgoing populations 1, 3 and -1 for the incoming 2, 4.
+__device__ __forceinline__ float4 a_change_x(const float4 g, const float4 P, float sdinv, float rg) {
+  const float re = P.w * rg;
+  return axpy(sdinv, f4(P.x * P.y, P.w, 0.0f, P.y * re), g);
+}
+__device__ __forceinline__ float4 a_change_y(const float4 g, const float4 P, float sdinv, float rg) {
+  const float re = P.w * rg;
+  return axpy(sdinv, f4(P.x * P.z, 0.0f, P.w, P.z * re), g);
+}
+
+// theta_f of face (L, R) and theta_f d_f in L's and R's frames; gL, gR are the
+// face's outgoing part of L and incoming part of R, already at a_n.
+__device__ __forceinline__ float face_theta(const float4 PL, const float4 PR, const float4 gL, const float4 gR,
+                                            const float4 UL, const float2 BL, const float4 UR, const float2 BR,
+                                            bool bL, bool bR, int limiter, const Ctx& k, float4& tdL, float4& tdR) {
+  float th;
+  float4 dL = f4(0.f, 0.f, 0.f, 0.f), dR = dL;
+  if ((bL && bR) || limiter == 0) {
+    th = 0.0f;
+  } else {
+    dL = d_in_L(gL, gR, PL, PR);
+    dR = d_in_R(gL, gR, PL, PR);
+    if (limiter == 1) {
+      th = 1.0f;
+    } else {
+      const float tL = bL ? 1.0f : theta_star(UL, scale(-4.f, dL), BL, k.eps, k.gm1, k.rg);
+      const float tR = bR ? 1.0f : theta_star(UR, scale(4.f, dR), BR, k.eps, k.gm1, k.rg);
+      th = fminf(tL, tR);
+    }
+  }
+  tdL = scale(th, dL);
+  tdR = scale(th, dR);
+  return th;
+}
+
+// P4 of an interior cell: Eq. (vlbm5) regrouped per face in the cell's frame,
+// the new nodal state (returned) and its four new rest-frame non-equilibrium
+// parts (Eqs. (vlbm1)-(vlbm4)), written at dst + off.  src.g(k) are the
+// cell's own parts at a_n, src.mk(k) its kept Maxwellians; tdRW, tdLE, tdRS,
+// tdLN the faces' theta_f d_f in this cell's frame.  Sets bit 1 / 2 of flags on a non-positive / non-finite
+// result; otherwise raises lam to the node's max(|v1|, |v2|) + c.
+// The kept Maxwellians and the cell's parts are fetched through src.mk(k) and
+// src.g(k) where they are used (k = 0..3), which keeps them out of registers
+// until then.
+template <class Src>
+__device__ __forceinline__ float4 update_cell(float4* __restrict__ dst, size_t plane, size_t off, const float4 Pc,
+                                              const float4 ULF, float thW, const float4 tdRW, float thE,
+                                              const float4 tdLE, float thS, const float4 tdRS, float thN,
+                                              const float4 tdLN, const Src& src, const Ctx& k, float& lam,
+                                              int& flags) {
+  const float4 U = add(sub(add(ULF, tdRW), tdLE), sub(tdRS, tdLN));
+  // new nodal state (rest frame of the old velocity -> primitive)
+  const float rn = U.x;
+  const float inv = __fdividef(1.0f, rn);
+  const float dv1 = U.y * inv, dv2 = U.z * inv;
+  const float ren = fmaf(-0.5f, fmaf(U.y, dv1, U.z * dv2), U.w);
+  const float pn = k.gm1 * ren;
+  const float wn1 = Pc.y + dv1, wn2 = Pc.z + dv2;
+  const float4 Pn = f4(rn, wn1, wn2, pn);
+  dst[off] = Pn;
+  int fl = 0;
+  if (!(rn > 0.0f) || !(pn > 0.0f)) fl |= 1;
+  if (!(fabsf(wn1) + fabsf(wn2) + rn + pn < __int_as_float(0x7f800000))) fl |= 2;
+  // lambda, rounded up by 2^-20 so that a_{n+1} >= 2 lambda despite the
+  // approximate reciprocal
+  if (!fl) lam = fmaxf(lam, (fmaxf(fabsf(wn1), fabsf(wn2)) + sqrtf(k.gamma * pn * inv)) * (1.0f + 0x1p-20f));
+  flags |= fl;
+  // g_k^{n+1} = M_k(u_X) - theta_f g_k(X) - M_k(u^{n+1}), X the upwind node,
+  // formed in the cell's old frame and boosted once to the new one.  In that
+  // frame B g_1(W) = g_2(c) - d_W (the face's d seen by c), and likewise for
+  // the other three faces.
+  const float dw1 = wn1 - Pc.y, dw2 = wn2 - Pc.z;
+  const float4 cU = scale(k.c1, U);
+  const float4 Fx = scale(k.h, xflux(U, dv1, dv2, pn, Pc.y));
+  const float4 Fy = scale(k.h, yflux(U, dv1, dv2, pn, Pc.z));
+  float4 X;
+  X = add(axpy(-thW, src.g(1), sub(src.mk(0), add(cU, Fx))), tdRW);
+  dst[1 * plane + off] = boost(X, dw1, dw2);
+  X = sub(axpy(-thE, src.g(0), sub(src.mk(1), sub(cU, Fx))), tdLE);
+  dst[2 * plane + off] = boost(X, dw1, dw2);
+  X = add(axpy(-thS, src.g(3), sub(src.mk(2), add(cU, Fy))), tdRS);
+  dst[3 * plane + off] = boost(X, dw1, dw2);
+  X = sub(axpy(-thN, src.g(2), sub(src.mk(3), sub(cU, Fy))), tdLN);
+  dst[4 * plane + off] = boost(X, dw1, dw2);
+  return Pn;
+}
+
+// Boundary writes owned by interior cell (gi, gj) (Eqs. (inletBC),
+// (outletBC), (transverseBC)): zero-gradient copies of its new state with
+// equilibrium populations (g' = 0) into the outlet column and the first / last
+// rows next to it, and, in the first interior column, the inlet datum of its
+// row (and of the corner rows) as FP32 primitives with equilibrium populations.
+__device__ __forceinline__ void boundary_writes(float4* __restrict__ dst, size_t plane, size_t off, int gi, int gj,
+                                                int nx, int ny, int nxp, const float4 Pn,
+                                                const float4* __restrict__ inl, const Ctx& k, float& lam) {
+  const bool cxl = gi == nx - 2, cyl = gj == 1, cyh = gj == ny - 2;
+  if (cxl || cyl || cyh) {
+    // targets: east (cxl), south / north (cyl / cyh), their east corners
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      const bool on = t == 0 ? cxl : t == 1 ? cyl : t == 2 ? (cyl && cxl) : t == 3 ? cyh : (cyh && cxl);
+      if (!on) continue;
+      const long long dj = t == 0 ? 0 : (t <= 2 ? -(long long)nxp : (long long)nxp);
+      const size_t o = off + dj + (t == 0 || t == 2 || t == 4 ? 1 : 0);
+      dst[o] = Pn;
+#pragma unroll
+      for (int q = 1; q <= 4; ++q) dst[q * plane + o] = f4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (gi == 1) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      // rows: this one, and the corner rows 0 / ny - 1 next to the sides
+      const int jj = r == 0 ? gj : r == 1 ? (gj == 1 ? 0 : -1) : (gj == ny - 2 ? ny - 1 : -1);
+      if (jj < 0) continue;
+      const float4 Pi = inl[jj];
+      const size_t oi = (size_t)jj * nxp;
+      dst[oi] = Pi;
+#pragma unroll
+      for (int q = 1; q <= 4; ++q) dst[q * plane + oi] = f4(0.f, 0.f, 0.f, 0.f);
+      lam = fmaxf(lam, (fmaxf(fabsf(Pi.y), fabsf(Pi.z)) + sqrtf(k.gamma * Pi.w / Pi.x)) * (1.0f + 0x1p-20f));
+    }
+  }
+}
+
+__device__ __forceinline__ Ctx make_ctx(const Launch& L, const RealState* rs) {
+  Ctx k;
+  k.gamma = L.pf.gamma;
+  k.gm1 = L.pf.gm1;
+  k.rg = L.pf.rg;
+  k.alpha = L.pf.alpha;
+  k.c1 = L.pf.c1;
+  k.h = rs->inv2a_f;
+  k.rel = L.pf.rel;
+  k.absb = L.pf.absb;
+  k.eps = L.pf.eps;
+  return k;
+}
+
 // Work unit u -> (level, realization, tile within the level); units run over
 // the tiles of realization 0 first, so CTAs in flight share halos through L2.
 __device__ __forceinline__ void decode_unit(const Launch& L, long long u, int& lvl, int& m, int& tile) {
@@ -243,16 +414,7 @@ __device__ __forceinline__ void compute_tile(const Launch& L, Boxes<TY>& Bx, Wor
   const size_t plane = D.plane;
   const int par = (int)(rs->steps & 1);
   float4* __restrict__ dst = reinterpret_cast<float4*>(D.lat) + ((size_t)(par ^ 1) * L.M + m) * D.real_stride;
-  Ctx k;
-  k.gamma = L.pf.gamma;
-  k.gm1 = L.pf.gm1;
-  k.rg = L.pf.rg;
-  k.alpha = L.pf.alpha;
-  k.c1 = L.pf.c1;
-  k.h = rs->inv2a_f;
-  k.rel = L.pf.rel;
-  k.absb = L.pf.absb;
-  k.eps = L.pf.eps;
+  const Ctx k = make_ctx(L, rs);
   const float dinv = rs->dinv2a_f;
   const int limiter = L.ph.limiter;
   const int i0 = 1 + (tile % D.tiles_x) * TX;
@@ -264,42 +426,27 @@ __device__ __forceinline__ void compute_tile(const Launch& L, Boxes<TY>& Bx, Wor
     const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
     if (gi < 1 || gi > nx - 2 || gj < 1 || gj > ny - 2) continue;
     const int hx = li + 1, hy = lj + 1;
-    const float4 Pc = Bx.P[hy][hx];
-    const float w1 = Pc.y, w2 = Pc.z;
-    float d1, d2;
-    const float4 PW = Bx.P[hy][hx - 1], PE = Bx.P[hy][hx + 1], PS = Bx.P[hy - 1][hx], PN = Bx.P[hy + 1][hx];
-    const float4 uW = boosted(PW, w1, w2, k, d1, d2);
-    const float4 M1 = axpy(k.h, xflux(uW, d1, d2, PW.w, w1), scale(k.c1, uW));
-    const float4 uE = boosted(PE, w1, w2, k, d1, d2);
-    const float4 M2 = axpy(-k.h, xflux(uE, d1, d2, PE.w, w1), scale(k.c1, uE));
-    const float4 uS = boosted(PS, w1, w2, k, d1, d2);
-    const float4 M3 = axpy(k.h, yflux(uS, d1, d2, PS.w, w2), scale(k.c1, uS));
-    const float4 uN = boosted(PN, w1, w2, k, d1, d2);
-    const float4 M4 = axpy(-k.h, yflux(uN, d1, d2, PN.w, w2), scale(k.c1, uN));
-    float4 U = add(add(M1, M2), add(M3, M4));
-    if (k.alpha != 0.0f) U = add(U, f4(k.alpha * Pc.x, 0.0f, 0.0f, (k.alpha * Pc.w) * k.rg));
+    float4 U, M1, M2, M3, M4;
+    float2 B;
+    node_p2(Bx.P[hy][hx], Bx.P[hy][hx - 1], Bx.P[hy][hx + 1], Bx.P[hy - 1][hx], Bx.P[hy + 1][hx], k, U, B, M1, M2,
+            M3, M4);
     W.U[lj][li] = U;
+    W.B[lj][li] = B;
     if (li >= 1 && li <= TX && lj >= 1 && lj <= TY) {
       W.Mk[0][lj - 1][li - 1] = M1;
       W.Mk[1][lj - 1][li - 1] = M2;
       W.Mk[2][lj - 1][li - 1] = M3;
       W.Mk[3][lj - 1][li - 1] = M4;
     }
-    const float lo = fminf(fminf(Pc.x, fminf(PW.x, PE.x)), fminf(fminf(PS.x, PN.x), U.x));
-    const float hi = fmaxf(fmaxf(Pc.x, fmaxf(PW.x, PE.x)), fmaxf(fmaxf(PS.x, PN.x), U.x));
-    const float delta = fmaf(k.rel, hi - lo, k.absb);
-    W.B[lj][li] = make_float2(lo - delta, hi + delta);
   }
   __syncthreads();
 
   // ---- P3: faces -------------------------------------------------------------
   // Thread (lx, ly) owns the west and south faces of its cell; the east faces
   // of the last column and the north faces of the top row go to the first
-  // warps.  A face brings its two non-equilibrium parts to a_n (the exact
-  // change B_v F(u) (1/2a_{n-1} - 1/2a_n) of the equilibrium, with
-  // B_v f(u) = (rho v1, p, 0, v1 rho e), B_v g(u) = (rho v2, 0, p, v2 rho e)),
-  // writes them back (each is used by this face alone), and stores theta_f
-  // and theta_f d_f in both cells' frames.
+  // warps.  A face brings its two non-equilibrium parts to a_n, writes them
+  // back (each is used by this face alone), and stores theta_f and
+  // theta_f d_f in both cells' frames.
   {
     const int lx = tid % TX, ly = tid / TX;
     constexpr int NEXTRA = TY + TX;
@@ -343,39 +490,25 @@ __device__ __forceinline__ void compute_tile(const Launch& L, Boxes<TY>& Bx, Wor
       float4 gL = Bx.G[kout][gyL][gxL], gR = Bx.G[kin][gyR][gxR];
       if (dinv != 0.0f) {
         if (!bL) {
-          const float re = PL.w * k.rg;
-          gL = axpy(dinv, xdir ? f4(PL.x * PL.y, PL.w, 0.0f, PL.y * re) : f4(PL.x * PL.z, 0.0f, PL.w, PL.z * re), gL);
+          gL = xdir ? a_change_x(gL, PL, dinv, k.rg) : a_change_y(gL, PL, dinv, k.rg);
           Bx.G[kout][gyL][gxL] = gL;
         }
         if (!bR) {
-          const float re = PR.w * k.rg;
-          gR = axpy(-dinv, xdir ? f4(PR.x * PR.y, PR.w, 0.0f, PR.y * re) : f4(PR.x * PR.z, 0.0f, PR.w, PR.z * re), gR);
+          gR = xdir ? a_change_x(gR, PR, -dinv, k.rg) : a_change_y(gR, PR, -dinv, k.rg);
           Bx.G[kin][gyR][gxR] = gR;
         }
       }
-      float th;
-      float4 dL = f4(0.f, 0.f, 0.f, 0.f), dR = dL;
-      if ((bL && bR) || limiter == 0) {
-        th = 0.0f;
-      } else {
-        dL = d_in_L(gL, gR, PL, PR);
-        dR = d_in_R(gL, gR, PL, PR);
-        if (limiter == 1) {
-          th = 1.0f;
-        } else {
-          const float tL = bL ? 1.0f : theta_star(W.U[gyL][gxL], scale(-4.f, dL), W.B[gyL][gxL], k);
-          const float tR = bR ? 1.0f : theta_star(W.U[gyR][gxR], scale(4.f, dR), W.B[gyR][gxR], k);
-          th = fminf(tL, tR);
-        }
-      }
+      float4 tdL, tdR;
+      const float th = face_theta(PL, PR, gL, gR, W.U[gyL][gxL], W.B[gyL][gxL], W.U[gyR][gxR], W.B[gyR][gxR], bL,
+                                  bR, limiter, k, tdL, tdR);
       if (xdir) {
         W.thx[fb][fa] = th;
-        W.tdLx[fb][fa] = scale(th, dL);
-        W.tdRx[fb][fa] = scale(th, dR);
+        W.tdLx[fb][fa] = tdL;
+        W.tdRx[fb][fa] = tdR;
       } else {
         W.thy[fb][fa] = th;
-        W.tdLy[fb][fa] = scale(th, dL);
-        W.tdRy[fb][fa] = scale(th, dR);
+        W.tdLy[fb][fa] = tdL;
+        W.tdRy[fb][fa] = tdR;
       }
     }
   }
@@ -389,84 +522,18 @@ __device__ __forceinline__ void compute_tile(const Launch& L, Boxes<TY>& Bx, Wor
     const int gi = i0 + lx, gj = j0 + ly;
     if (gi <= nx - 2 && gj <= ny - 2) {
       const int cx = lx + 1, cy = ly + 1;
-      const float4 Pc = Bx.P[ly + 2][lx + 2];
-      const float thW = W.thx[ly][lx], thE = W.thx[ly][lx + 1], thS = W.thy[ly][lx], thN = W.thy[ly + 1][lx];
-      const float4 tdRW = W.tdRx[ly][lx], tdLE = W.tdLx[ly][lx + 1];
-      const float4 tdRS = W.tdRy[ly][lx], tdLN = W.tdLy[ly + 1][lx];
-      // Eq. (vlbm5) regrouped per face: U_LF + sum_f s theta_f d_f, cell frame
-      const float4 U = add(sub(add(W.U[cy][cx], tdRW), tdLE), sub(tdRS, tdLN));
-      // new nodal state (rest frame of the old velocity -> primitive)
-      const float rn = U.x;
-      const float inv = __fdividef(1.0f, rn);
-      const float dv1 = U.y * inv, dv2 = U.z * inv;
-      const float ren = fmaf(-0.5f, fmaf(U.y, dv1, U.z * dv2), U.w);
-      const float pn = k.gm1 * ren;
-      const float wn1 = Pc.y + dv1, wn2 = Pc.z + dv2;
-      const float4 Pn = f4(rn, wn1, wn2, pn);
       const size_t off = (size_t)gj * nxp + gi;
-      dst[off] = Pn;
-      if (!(rn > 0.0f) || !(pn > 0.0f)) flags |= 1;
-      if (!(fabsf(wn1) + fabsf(wn2) + rn + pn < __int_as_float(0x7f800000))) flags |= 2;
-      // lambda, rounded up by 2^-20 so that a_{n+1} >= 2 lambda despite the
-      // approximate reciprocal
-      if (!flags) lam = (fmaxf(fabsf(wn1), fabsf(wn2)) + sqrtf(k.gamma * pn * inv)) * (1.0f + 0x1p-20f);
-      // New non-equilibrium parts, Eqs. (vlbm1)-(vlbm4):
-      // g_k^{n+1} = M_k(u_X) - theta_f g_k(X) - M_k(u^{n+1}), X the upwind node,
-      // formed in the cell's old frame and boosted once to the new one.  In
-      // that frame B g_1(W) = g_2(c) - d_W (the face's d seen by c), and
-      // likewise for the other three faces.
-      {
-        const float dw1 = wn1 - Pc.y, dw2 = wn2 - Pc.z;
-        const float4 cU = scale(k.c1, U);
-        const float4 Fx = scale(k.h, xflux(U, dv1, dv2, pn, Pc.y));
-        const float4 Fy = scale(k.h, yflux(U, dv1, dv2, pn, Pc.z));
-        const float4 g1c = Bx.G[0][cy][cx], g2c = Bx.G[1][cy][cx], g3c = Bx.G[2][cy][cx], g4c = Bx.G[3][cy][cx];
-        float4 X;
-        X = add(axpy(-thW, g2c, sub(W.Mk[0][ly][lx], add(cU, Fx))), tdRW);
-        dst[1 * plane + off] = boost(X, dw1, dw2);
-        X = sub(axpy(-thE, g1c, sub(W.Mk[1][ly][lx], sub(cU, Fx))), tdLE);
-        dst[2 * plane + off] = boost(X, dw1, dw2);
-        X = add(axpy(-thS, g4c, sub(W.Mk[2][ly][lx], add(cU, Fy))), tdRS);
-        dst[3 * plane + off] = boost(X, dw1, dw2);
-        X = sub(axpy(-thN, g3c, sub(W.Mk[3][ly][lx], sub(cU, Fy))), tdLN);
-        dst[4 * plane + off] = boost(X, dw1, dw2);
-      }
-      // zero-gradient copies: nodal state, equilibrium populations (g' = 0)
-      const bool cxl = gi == nx - 2, cyl = gj == 1, cyh = gj == ny - 2;
-      if (cxl || cyl || cyh) {
-        const float4 z = f4(0.f, 0.f, 0.f, 0.f);
-        size_t outs[5];
-        int no = 0;
-        if (cxl) outs[no++] = off + 1;
-        if (cyl) {
-          outs[no++] = off - nxp;
-          if (cxl) outs[no++] = off - nxp + 1;
-        }
-        if (cyh) {
-          outs[no++] = off + nxp;
-          if (cxl) outs[no++] = off + nxp + 1;
-        }
-        for (int o = 0; o < no; ++o) {
-          dst[outs[o]] = Pn;
-          for (int q = 1; q <= 4; ++q) dst[q * plane + outs[o]] = z;
-        }
-      }
-      // inlet column (Dirichlet datum as FP32 primitives, equilibrium populations)
-      if (gi == 1) {
-        const float4* inl = D.inlet_f + (size_t)m * ny;
-        int rows[3] = {gj, -1, -1};
-        if (gj == 1) rows[1] = 0;
-        if (gj == ny - 2) rows[2] = ny - 1;
-        for (int r = 0; r < 3; ++r) {
-          const int jj = rows[r];
-          if (jj < 0) continue;
-          const float4 Pi = inl[jj];
-          const size_t oi = (size_t)jj * nxp;
-          dst[oi] = Pi;
-          for (int q = 1; q <= 4; ++q) dst[q * plane + oi] = f4(0.f, 0.f, 0.f, 0.f);
-          lam = fmaxf(lam, (fmaxf(fabsf(Pi.y), fabsf(Pi.z)) + sqrtf(k.gamma * Pi.w / Pi.x)) * (1.0f + 0x1p-20f));
-        }
-      }
+      struct {
+        const Boxes<TY>& bx;
+        const Work<TY>& w;
+        int lx, ly;
+        __device__ float4 mk(int q) const { return w.Mk[q][ly][lx]; }
+        __device__ float4 g(int q) const { return bx.G[q][ly + 1][lx + 1]; }
+      } src{Bx, W, lx, ly};
+      const float4 Pn = update_cell(dst, plane, off, Bx.P[ly + 2][lx + 2], W.U[cy][cx], W.thx[ly][lx],
+                                    W.tdRx[ly][lx], W.thx[ly][lx + 1], W.tdLx[ly][lx + 1], W.thy[ly][lx],
+                                    W.tdRy[ly][lx], W.thy[ly + 1][lx], W.tdLy[ly + 1][lx], src, k, lam, flags);
+      boundary_writes(dst, plane, off, gi, gj, nx, ny, nxp, Pn, D.inlet_f + (size_t)m * ny, k, lam);
     }
   }
   // lambda >= 0: its FP32 bit pattern orders like an unsigned integer
@@ -593,10 +660,191 @@ __global__ void __launch_bounds__(TX* TY, 1) step_mixed_persistent_kernel(const 
   }
 }
 
-// Variants: {tile rows, persistent}.
-constexpr int kRows[] = {4, 8, 8};
-constexpr bool kPersistent[] = {false, false, true};
-constexpr int kNumVariants = 3;
+// ---- warp-marching design ----------------------------------------------------
+// A warp owns a strip of kMW interior columns (lanes 1..kMW; lanes 0 and 31
+// hold the halo columns) and marches up D.wrows rows of it.  Nodal states and
+// non-equilibrium parts go straight from global memory into registers, each
+// lane loading its own column (512 contiguous bytes per row and plane for the
+// warp); x-neighbours come by warp shuffle.  The window in registers holds
+// three rows of nodal states, U_LF and bounds of the current and the next row,
+// and the face between them; the Maxwellians kept for the next row wait in
+// the lane's own shared-memory slot.  A warp never waits for another warp.
+constexpr int kMW = 30;      // columns updated per warp
+constexpr int kMNW = 4;      // warps per CTA
+constexpr int kMarchRows = 25;  // target rows per warp
+
+__device__ __forceinline__ float4 shfl_up4(const float4 v) {
+  return f4(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1),
+            __shfl_up_sync(0xffffffffu, v.z, 1), __shfl_up_sync(0xffffffffu, v.w, 1));
+}
+__device__ __forceinline__ float4 shfl_down4(const float4 v) {
+  return f4(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1),
+            __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
+}
+__device__ __forceinline__ float2 shfl_down2(const float2 v) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+}
+
+// blockIdx.x = (strip, row chunk) over all levels, blockIdx.y = realization;
+// MINB CTAs per SM bound the registers.
+template <int MINB>
+__global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const __grid_constant__ Launch L) {
+  __shared__ float4 smk[2][4][kMNW][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int unit = blockIdx.x, lvl = 0;
+  while (lvl + 1 < L.nlevels && unit >= L.lv[lvl + 1].tile_begin) ++lvl;
+  unit -= L.lv[lvl].tile_begin;
+  const int m = blockIdx.y;
+  const LevelDesc& D = L.lv[lvl];
+  RealState* rs = D.rs + m;
+  if (!rs->active) return;
+  const int nx = D.nx, ny = D.ny, nxp = D.nx_pad;
+  const int ra = 1 + ((unit / D.tiles_x) * kMNW + wid) * D.wrows;
+  const int rb = min(ra + D.wrows - 1, ny - 2);
+  if (ra > rb) return;
+  // lane l holds column x0 - 1 + l of the strip starting at x0 = 1 + kMW * strip
+  const int c = (unit % D.tiles_x) * kMW + lane;
+  const size_t plane = D.plane;
+  const int par = (int)(rs->steps & 1);
+  const float4* __restrict__ src =
+      reinterpret_cast<const float4*>(D.lat) + ((size_t)par * L.M + m) * D.real_stride;
+  float4* __restrict__ dst = reinterpret_cast<float4*>(D.lat) + ((size_t)(par ^ 1) * L.M + m) * D.real_stride;
+  const float4* __restrict__ inl = D.inlet_f + (size_t)m * ny;
+  const Ctx k = make_ctx(L, rs);
+  const float dinv = rs->dinv2a_f;
+  const int limiter = L.ph.limiter;
+  const bool colin = c >= 1 && c <= nx - 2;          // interior column
+  const bool colin_e = c + 1 <= nx - 2;              // east neighbour's column interior
+  const bool upd = lane >= 1 && lane <= kMW && colin;  // this lane updates cells
+  const int cl = min(c, nx - 1);
+  const int cf = lane == 0 ? c - 1 : c + 1;  // the halo lanes' far column
+  const bool far = (lane == 0 || lane == 31) && cf >= 0 && cf <= nx - 1;
+  const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
+  auto ldP = [&](int q) { return q >= 0 && q <= ny - 1 ? __ldg(src + (size_t)q * nxp + cl) : z4; };
+  auto ldF = [&](int q) { return far && q >= 0 && q <= ny - 1 ? __ldg(src + (size_t)q * nxp + cf) : z4; };
+  auto ldG = [&](int kk, int q) {
+    return q >= 0 && q <= ny - 1 ? __ldg(src + (size_t)(kk + 1) * plane + (size_t)q * nxp + cl) : z4;
+  };
+  auto inner = [&](int q) { return colin && q >= 1 && q <= ny - 2; };
+  auto west = [&](const float4 P, const float4 F) {
+    const float4 w = shfl_up4(P);
+    return lane == 0 ? F : w;
+  };
+  auto east = [&](const float4 P, const float4 F) {
+    const float4 e = shfl_down4(P);
+    return lane == 31 ? F : e;
+  };
+  auto keep = [&](int q, const float4 M1, const float4 M2, const float4 M3, const float4 M4) {
+    smk[q & 1][0][wid][lane] = M1;
+    smk[q & 1][1][wid][lane] = M2;
+    smk[q & 1][2][wid][lane] = M3;
+    smk[q & 1][3][wid][lane] = M4;
+  };
+
+  // ---- warm-up: rows ra - 1 and ra, and the face between them ----------------
+  float4 M1, M2, M3, M4;
+  float4 Pq = ldP(ra), Pq1 = ldP(ra + 1), Fq1 = ldF(ra + 1);
+  float4 Uq = z4, PEq;
+  float2 Bq = make_float2(0.f, 0.f);
+  float thS;
+  float4 tdRS, g4q;
+  {
+    const float4 Pm2 = ldP(ra - 2), Pm = ldP(ra - 1), Fm = ldF(ra - 1), Fq = ldF(ra);
+    float4 Um = z4;
+    float2 Bm = make_float2(0.f, 0.f);
+    const float4 PWm = west(Pm, Fm), PEm = east(Pm, Fm);
+    if (inner(ra - 1)) node_p2(Pm, PWm, PEm, Pm2, Pq, k, Um, Bm, M1, M2, M3, M4);
+    const float4 PWq = west(Pq, Fq);
+    PEq = east(Pq, Fq);
+    if (inner(ra)) {
+      node_p2(Pq, PWq, PEq, Pm, Pq1, k, Uq, Bq, M1, M2, M3, M4);
+      keep(ra, M1, M2, M3, M4);
+    }
+    const bool bm = !inner(ra - 1), bq = !inner(ra);
+    float4 g3m = ldG(2, ra - 1);
+    g4q = ldG(3, ra);
+    if (dinv != 0.0f) {
+      if (!bm) g3m = a_change_y(g3m, Pm, dinv, k.rg);
+      if (!bq) g4q = a_change_y(g4q, Pq, -dinv, k.rg);
+    }
+    float4 unused;
+    thS = face_theta(Pm, Pq, g3m, g4q, Um, Bm, Uq, Bq, bm, bq, limiter, k, unused, tdRS);
+  }
+
+  // ---- march -----------------------------------------------------------------
+  float lam = 0.0f;
+  int flags = 0;
+  for (int q = ra; q <= rb; ++q) {
+    const float4 Pq2 = ldP(q + 2), Fq2 = ldF(q + 2);
+    float4 G1 = ldG(0, q), G2 = ldG(1, q), G3 = ldG(2, q), g4n = ldG(3, q + 1);
+    // P2 of row q + 1
+    float4 U1 = z4;
+    float2 B1 = make_float2(0.f, 0.f);
+    const float4 PW1 = west(Pq1, Fq1), PE1 = east(Pq1, Fq1);
+    const bool bq = !colin, b1 = !inner(q + 1);
+    if (!b1) {
+      node_p2(Pq1, PW1, PE1, Pq, Pq2, k, U1, B1, M1, M2, M3, M4);
+      keep(q + 1, M1, M2, M3, M4);
+    }
+    // this row's parts 1..3 and the next row's part 4 at a_n
+    if (dinv != 0.0f) {
+      if (!bq) {
+        G1 = a_change_x(G1, Pq, dinv, k.rg);
+        G2 = a_change_x(G2, Pq, -dinv, k.rg);
+        G3 = a_change_y(G3, Pq, dinv, k.rg);
+      }
+      if (!b1) g4n = a_change_y(g4n, Pq1, -dinv, k.rg);
+    }
+    // north face of row q (= south face of row q + 1)
+    float4 tdLN, tdRN;
+    const float thN = face_theta(Pq, Pq1, G3, g4n, Uq, Bq, U1, B1, bq, b1, limiter, k, tdLN, tdRN);
+    // east face (R = lane + 1); the west face comes from lane - 1
+    const float4 gR = shfl_down4(G2), UR = shfl_down4(Uq);
+    const float2 BR = shfl_down2(Bq);
+    float4 tdLE, tdRE;
+    const float thE = face_theta(Pq, PEq, G1, gR, Uq, Bq, UR, BR, bq, !colin_e, limiter, k, tdLE, tdRE);
+    const float thW = __shfl_up_sync(0xffffffffu, thE, 1);
+    const float4 tdRW = shfl_up4(tdRE);
+    if (upd) {
+      struct {
+        const float4 (*mk_)[kMNW][32];
+        int wid, lane;
+        float4 g0, g1, g2, g3;
+        __device__ float4 mk(int i) const { return mk_[i][wid][lane]; }
+        __device__ float4 g(int i) const { return i == 0 ? g0 : i == 1 ? g1 : i == 2 ? g2 : g3; }
+      } cell{smk[q & 1], wid, lane, G1, G2, G3, g4q};
+      const size_t off = (size_t)q * nxp + c;
+      const float4 Pn =
+          update_cell(dst, plane, off, Pq, Uq, thW, tdRW, thE, tdLE, thS, tdRS, thN, tdLN, cell, k, lam, flags);
+      boundary_writes(dst, plane, off, c, q, nx, ny, nxp, Pn, inl, k, lam);
+    }
+    Pq = Pq1;
+    PEq = PE1;
+    Pq1 = Pq2;
+    Fq1 = Fq2;
+    Uq = U1;
+    Bq = B1;
+    g4q = g4n;
+    thS = thN;
+    tdRS = tdRN;
+  }
+  // lambda >= 0: its FP32 bit pattern orders like an unsigned integer
+  unsigned lb = __float_as_uint(lam);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lb = max(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+    flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+  }
+  if (lane == 0) {
+    atomicMax(&rs->lam_next_bits, lam_to_bits((double)__uint_as_float(lb)));
+    if (flags) atomicOr(&rs->flags, flags);
+  }
+}
+
+// Variants: 32 x 4 tiles, 32 x 8 tiles, persistent 32 x 8 tiles, warp march
+// with 4 or 5 CTAs of 4 warps per SM.
+constexpr const char* kVariantNames[] = {"tile32x4", "tile32x8", "persistent32x8", "march30x4w", "march30x5w"};
+constexpr int kNumVariants = 5;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -688,11 +936,31 @@ cudaError_t launch_persistent(Launch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Strips of kMW columns; rows split into chunks of kMNW warps with about
+// kMarchRows rows per warp.
+template <int MINB>
+cudaError_t launch_march(Launch& L, cudaStream_t s) {
+  int units = 0;
+  for (int l = 0; l < L.nlevels; ++l) {
+    LevelDesc& D = L.lv[l];
+    const int rows = D.ny - 2;
+    const int chunks = (rows + kMNW * kMarchRows - 1) / (kMNW * kMarchRows);
+    D.tiles_x = (D.nx - 2 + kMW - 1) / kMW;
+    D.tiles_y = chunks;
+    D.wrows = (rows + chunks * kMNW - 1) / (chunks * kMNW);
+    D.tile_begin = units;
+    units += D.tiles_x * D.tiles_y;
+  }
+  L.total_tiles = units;
+  step_mixed_march_kernel<MINB><<<dim3(units, L.M), kMNW * 32, 0, s>>>(L);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int mixed_variants() { return kNumVariants; }
-int mixed_variant_rows(int v) { return kRows[v]; }
-bool mixed_variant_persistent(int v) { return kPersistent[v]; }
+const char* mixed_variant_name(int v) { return v >= 0 && v < kNumVariants ? kVariantNames[v] : "?"; }
 
 cudaError_t launch_step_mixed(const Launch& Lin, int variant, cudaStream_t s) {
   static thread_local Launch L;  // large (TMA descriptors): kept off the stack
@@ -702,8 +970,12 @@ cudaError_t launch_step_mixed(const Launch& Lin, int variant, cudaStream_t s) {
       return launch_tile<4>(L, s);
     case 1:
       return launch_tile<8>(L, s);
-    default:
+    case 2:
       return launch_persistent<8>(L, s);
+    case 3:
+      return launch_march<4>(L, s);
+    default:
+      return launch_march<5>(L, s);
   }
 }
 

@@ -28,11 +28,11 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONPOSITIVE", 5: "
 
 EXPORTED = [
     "vlbm_default_relax", "vlbm_default_perturb", "vlbm_create", "vlbm_init_ensemble",
-    "vlbm_init_ensemble_block", "vlbm_kernel_launches", "vlbm_step",
+    "vlbm_init_ensemble_block", "vlbm_init_ensemble_samples", "vlbm_kernel_launches", "vlbm_step",
     "vlbm_advance_to", "vlbm_moments", "vlbm_density", "vlbm_time", "vlbm_sync", "vlbm_get_state",
     "vlbm_set_state", "stats_w1_mean_std", "stats_error_functionals", "stats_error_functionals_noalloc",
     "stats_quantiles", "stats_histogram",
-    "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_destroy",
+    "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_step_design", "vlbm_destroy",
 ]
 
 
@@ -89,6 +89,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "vlbm_create": ([p, i, d, p, p, p, i, p, ALLOC_FN, FREE_FN, p, ctypes.POINTER(p)], i),
         "vlbm_init_ensemble": ([p, u64, i, p], i),
         "vlbm_init_ensemble_block": ([p, u64, i, i, p], i),
+        "vlbm_init_ensemble_samples": ([p, p, i, p], i),
         "vlbm_kernel_launches": ([], ctypes.c_ulonglong),
         "vlbm_step": ([p, i], i),
         "vlbm_advance_to": ([p, d], i),
@@ -106,6 +107,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "vlbm_save": ([p, p, ctypes.POINTER(ctypes.c_size_t)], i),
         "vlbm_load": ([p, p, ctypes.c_size_t], i),
         "vlbm_last_error": ([p], ctypes.c_char_p),
+        "vlbm_step_design": ([p, p, ctypes.POINTER(ctypes.c_char_p), p], i),
         "vlbm_destroy": ([p], None),
     }
     for name, (args, res) in sig.items():
@@ -264,6 +266,21 @@ class Ensemble:
         self._call(self.lib.vlbm_init_ensemble_block, seed, m_begin, M, ctypes.byref(p))
         self.M = M
 
+    def init_samples(self, xi, perturb: PerturbParams = PerturbParams()):
+        """Initialises M = xi.shape[0] realizations from given KL coefficients:
+        row r holds Y_1..Y_K, Z_1..Z_K in [-1, 1].  xi is a float64 numpy
+        array, or a CPU (pinned or pageable) or CUDA torch tensor."""
+        if isinstance(xi, np.ndarray):
+            xi = torch.from_numpy(np.ascontiguousarray(xi, dtype=np.float64))
+        if xi.dtype != torch.float64 or not xi.is_contiguous() or xi.dim() != 2:
+            raise ValueError("xi must be a contiguous float64 matrix [M, 2K]")
+        p = perturb.c()
+        if xi.shape[1] != 2 * p.K:
+            raise ValueError(f"xi has {xi.shape[1]} columns; 2K = {2 * p.K}")
+        self._xi_keep = xi  # a pinned host buffer is read asynchronously
+        self._call(self.lib.vlbm_init_ensemble_samples, _ptr(xi), int(xi.shape[0]), ctypes.byref(p))
+        self.M = int(xi.shape[0])
+
     def step(self, n: int = 1):
         self._call(self.lib.vlbm_step, n)
 
@@ -297,6 +314,13 @@ class Ensemble:
 
     def sync(self):
         self._call(self.lib.vlbm_sync)
+
+    def step_design(self):
+        """(index, name, count) of the mixed step kernel's launch design; index
+        -1 before the first step or for FP64."""
+        idx, cnt, name = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_char_p()
+        _check(self.lib.vlbm_step_design(self.ctx, ctypes.byref(idx), ctypes.byref(name), ctypes.byref(cnt)), self.ctx)
+        return idx.value, name.value.decode(), cnt.value
 
     def get_state(self, level: int = 0, m0: int = 0, count: int | None = None, pops: bool = True):
         count = self._count(m0, count)

@@ -7,6 +7,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2605_25282_gb300 import vlbm
@@ -52,6 +53,8 @@ def _create(levels, gamma=5 / 3, jet=None, amb=None, relax=None, precision=0):
     (dict(levels=[vlbm.Grid(200, 100, 2.5, -0.5, 0.5)]), "square"),
     (dict(levels=[vlbm.jet_grid(200, 100)], gamma=1.0), "gamma"),
     (dict(levels=[vlbm.jet_grid(200, 100)], jet=vlbm.Prim(-5.0, 800.0, 0.0, 0.4127)), "rho > 0"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], amb=vlbm.Prim(float("inf"), 0.0, 0.0, 0.4127)), "finite"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], jet=vlbm.Prim(5.0, float("nan"), 0.0, 0.4127)), "finite"),
     (dict(levels=[vlbm.jet_grid(200, 100)], precision=7), "precision"),
     (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(1.0, 1.0, 2, 0.1, 0.0, 1e-13)), "alpha"),
     (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(0.0, 0.5, 2, 0.1, 0.0, 1e-13)), "kappa"),
@@ -84,3 +87,26 @@ def test_null_context_calls_fail_cleanly():
     assert lib.vlbm_sync(None) == 1
     assert lib.vlbm_last_error(None)
     lib.vlbm_destroy(None)
+
+
+def test_init_samples_rejects_out_of_range_host_values_before_device_work():
+    lib = vlbm.load_library()
+    arr = (vlbm.Grid * 1)(vlbm.jet_grid(16, 8))
+    jet, amb = vlbm.Prim(5.0, 800.0, 0.0, 0.4127), vlbm.Prim(0.5, 0.0, 0.0, 0.4127)
+    ctx = ctypes.c_void_p()
+    code = lib.vlbm_create(arr, 1, 5 / 3, ctypes.byref(jet), ctypes.byref(amb), None, 1, None,
+                           vlbm.ALLOC_FN(0), vlbm.FREE_FN(0), None, ctypes.byref(ctx))
+    assert code == 0, lib.vlbm_last_error(None)
+    try:
+        p = vlbm.PerturbParams(K=3).c()
+        for bad in (1.5, float("nan"), -1.0000001):
+            xi = np.zeros((2, 6))
+            xi[1, 4] = bad
+            code = lib.vlbm_init_ensemble_samples(ctx, xi.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(p))
+            assert code == 1 and "xi[10]" in lib.vlbm_last_error(ctx).decode(), bad
+        assert lib.vlbm_init_ensemble_samples(ctx, None, 2, ctypes.byref(p)) == 1
+        idx, name, cnt = ctypes.c_int(7), ctypes.c_char_p(), ctypes.c_int(0)
+        assert lib.vlbm_step_design(ctx, ctypes.byref(idx), ctypes.byref(name), ctypes.byref(cnt)) == 0
+        assert idx.value == -1 and name.value == b"none" and cnt.value >= 5
+    finally:
+        lib.vlbm_destroy(ctx)
