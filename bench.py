@@ -166,7 +166,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
 
-    from paper_2605_25282_gb300 import vlbm
+    from paper_2605_25282_gb300 import sharded, vlbm
 
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
@@ -213,7 +213,11 @@ def run_ours(args):
             ev[1].record(stream)
         ens.density(0, out=dens_a)
         ens.density(1, out=dens_b)
-        st = vlbm.stats_w1_mean_std(dens_a, dens_b, stream=stream)
+        if dist is None:
+            st = vlbm.stats_w1_mean_std(dens_a, dens_b, stream=stream)
+        else:
+            # statistics over the realizations of every rank: one row-block all-to-all
+            st = sharded.gpu_statistics(dens_a, dens_b)
         if e2e:
             for h, k in zip(host_out, ("mean_a", "std_a", "mean_b", "std_b", "w1")):
                 h.copy_(st[k], non_blocking=True)

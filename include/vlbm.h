@@ -199,6 +199,18 @@ int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const v
                       int b_is_f32, int nxb, int nyb, int M, double* mean_a, double* std_a,
                       double* mean_b, double* std_b, double* w1, void* cuda_stream);
 
+/* Sec. 3.3: the conservative restriction operator R, block averaging of each
+ * of the M fields ens [M][ny][nx] (device; FP32 when is_f32 != 0, else FP64)
+ * onto the coarse grid [M][ny/r][nx/r]: coarse cell (I, J) is the mean of
+ * fine cells (r I .. r I + r - 1, r J .. r J + r - 1), summed in FP64 (fine
+ * rows outer, columns inner, as in stats_w1_mean_std).  out (device) is FP32
+ * when out_is_f32 != 0, else FP64, and must not overlap ens.  r must divide
+ * nx and ny; 1 <= M <= 65535.  Asynchronous on cuda_stream (may be NULL).
+ * Comparing several levels on one common grid (the paper's protocol) is
+ * restricting each level onto it, then calling the statistics with r = 1. */
+int stats_restrict(const void* ens, int is_f32, int nx, int ny, int M, int r, void* out, int out_is_f32,
+                   void* cuda_stream);
+
 /* Sec. 3.3-3.4, Eqs. (mean), (std), (w1disc), (strongError): the error
  * functionals between ensemble a [M][nya][nxa] and ensemble b [M][nyb][nxb]
  * (b block-restricted onto a's grid as in stats_w1_mean_std), written to the

@@ -638,6 +638,18 @@ int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const v
   return VLBM_OK;
 }
 
+int stats_restrict(const void* ens, int is_f32, int nx, int ny, int M, int r, void* out, int out_is_f32,
+                   void* cuda_stream) {
+  if (!ens || !out) return fail(nullptr, VLBM_EINVAL, "ensemble and output pointers must be non-NULL");
+  if (nx < 1 || ny < 1 || M < 1 || r < 1) return fail(nullptr, VLBM_EINVAL, "nx, ny, M and r must be >= 1");
+  if (nx % r || ny % r) return fail(nullptr, VLBM_EINVAL, "r must divide nx and ny");
+  if (M > 65535) return fail(nullptr, VLBM_EINVAL, "M must be <= 65535");
+  cudaError_t e = restrict_launch(ens, is_f32 != 0, nx, ny, M, r, out, out_is_f32 != 0,
+                                  static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "restriction kernel");
+  return VLBM_OK;
+}
+
 int stats_error_functionals(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32,
                             int nxb, int nyb, int M, double* out, void* cuda_stream) {
   const char* why = "";

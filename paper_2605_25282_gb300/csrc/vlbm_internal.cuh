@@ -126,6 +126,10 @@ const char* mixed_variant_name(int variant);
 cudaError_t launch_step_mixed(const Launch& L, int variant, cudaStream_t s);
 
 // xi: NULL (Philox draws from seed, m_begin) or device [M][2K] given uniforms.
+// Block average of M fields [ny][nx] onto [ny / r][nx / r] (r divides both).
+cudaError_t restrict_launch(const void* ens, int is_f32, int nx, int ny, int M, int r, void* out, int out_f32,
+                            cudaStream_t s);
+
 cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, const double* xi,
                          cudaStream_t s);
 cudaError_t launch_init_state(const Launch& L, int precision, cudaStream_t s);

@@ -148,4 +148,41 @@ int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* 
   return VLBM_OK;
 }
 
+namespace {
+
+// One thread per (coarse cell, realization): the block average in the
+// summation order of stats_kernel (fine rows outer, fine columns inner).
+__global__ void restrict_kernel(const void* __restrict__ ens, int is_f32, int nx, int r, int nxc, int nyc,
+                                void* __restrict__ out, int out_f32) {
+  const int m = blockIdx.y;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nc = (long long)nxc * nyc;
+  if (cell >= nc) return;
+  const int I = (int)(cell % nxc), J = (int)(cell / nxc);
+  const size_t nf = (size_t)nc * r * r;
+  double s = 0.0;
+  for (int aa = 0; aa < r; ++aa)
+    for (int bb = 0; bb < r; ++bb)
+      s += load_sample(ens, is_f32, (size_t)m * nf + (size_t)(r * J + aa) * nx + (size_t)(r * I + bb));
+  const double v = s / (double)(r * r);
+  const size_t o = (size_t)m * nc + cell;
+  if (out_f32)
+    reinterpret_cast<float*>(out)[o] = (float)v;
+  else
+    reinterpret_cast<double*>(out)[o] = v;
+}
+
+}  // namespace
+
+cudaError_t restrict_launch(const void* ens, int is_f32, int nx, int ny, int M, int r, void* out, int out_f32,
+                            cudaStream_t s) {
+  const int nxc = nx / r, nyc = ny / r;
+  const long long nc = (long long)nxc * nyc;
+  if (nc == 0 || M == 0) return cudaSuccess;
+  restrict_kernel<<<dim3((unsigned)((nc + 255) / 256), (unsigned)M), 256, 0, s>>>(ens, is_f32, nx, r, nxc, nyc, out,
+                                                                                   out_f32);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace vlbm

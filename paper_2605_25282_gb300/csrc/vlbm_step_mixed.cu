@@ -41,6 +41,12 @@ namespace {
 
 constexpr int TX = 32;
 
+// Limits of theta_star at a node: density floor and ceiling, and the pressure
+// floor as kk = eps_p / (gamma - 1).
+struct Bnd {
+  float lo, hi, kk;
+};
+
 template <int TY>
 struct Boxes {
   static constexpr int HX = TX + 4, HY = TY + 4, GX = TX + 2, GY = TY + 2;
@@ -52,7 +58,7 @@ template <int TY>
 struct Work {
   static constexpr int GX = TX + 2, GY = TY + 2;
   float4 U[GY][GX];                  // U_LF in the node's own frame
-  float2 B[GY][GX];                  // relaxed density bounds lo - delta, hi + delta
+  Bnd B[GY][GX];                     // theta limits of the node (see node_p2)
   float4 Mk[4][TY][TX];              // B_vc M_k(u_upwind) of every tile cell (frame of the cell)
   float4 tdLx[TY][TX + 1], tdRx[TY][TX + 1];  // theta_f d_f in L's / R's frame, x faces
   float4 tdLy[TY + 1][TX], tdRy[TY + 1][TX];  // same, y faces
@@ -131,22 +137,17 @@ __device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float
 // cancellation in the pressure quadratic).  The floors eps_rho, eps_p are
 // min(value, max(eps_pos, 1e-5 value)) of the first-order state U0: the
 // relative margin keeps the final average admissible despite FP32 rounding.
-// theta = 1 is tested first, without any division (the common case).  The
-// constants come by value so that no context struct lives in local memory.
-__device__ float theta_star(const float4 U0, const float4 D, const float2 Bd, float eps, float gm1, float rg) {
-  const float er = fminf(U0.x, fmaxf(eps, 1e-5f * U0.x));
-  const float lower = fmaxf(er, Bd.x);
-  const float4 V = add(U0, D);
-  const float pLF = gm1 * fmaf(-0.5f, __fdividef(fmaf(U0.y, U0.y, U0.z * U0.z), U0.x), U0.w);
-  const float ep = fminf(pLF, fmaxf(eps, 1e-5f * pLF));
-  const float kk = ep * rg;
-  // q(theta) = rho E - |m|^2 / 2 - kk rho at theta = 1
-  if (V.x >= lower && V.x <= Bd.y && fmaf(V.x, V.w - kk, -0.5f * fmaf(V.y, V.y, V.z * V.z)) >= 0.0f) return 1.0f;
+// theta = 1 is tested first, inline and without any division (the common
+// case); the general case is a call.  The constants come by value so that no
+// context struct lives in local memory.
+__device__ __noinline__ float theta_star_general(const float4 U0, const float4 D, float lower, float hi_b,
+                                                 float kk) {
   float th = 1.0f;
-  if (V.x < lower) {
+  const float vx = U0.x + D.x;
+  if (vx < lower) {
     th = __fdividef(U0.x - lower, -D.x);
-  } else if (V.x > Bd.y) {
-    th = __fdividef(Bd.y - U0.x, D.x);
+  } else if (vx > hi_b) {
+    th = __fdividef(hi_b - U0.x, D.x);
   }
   th = fminf(fmaxf(th, 0.0f), 1.0f);
   const float C = fmaf(U0.x, U0.w - kk, -0.5f * fmaf(U0.y, U0.y, U0.z * U0.z));
@@ -168,6 +169,14 @@ __device__ float theta_star(const float4 U0, const float4 D, const float2 Bd, fl
     if (r < 0.0f) return 0.0f;
   }
   return fminf(fmaxf(r, 0.0f), th);
+}
+
+// b holds the node's limits, computed once per node by node_p2.
+__device__ __forceinline__ float theta_star(const float4 U0, const float4 D, const Bnd b) {
+  const float4 V = add(U0, D);
+  // q(theta) = rho E - |m|^2 / 2 - kk rho at theta = 1
+  if (V.x >= b.lo && V.x <= b.hi && fmaf(V.x, V.w - b.kk, -0.5f * fmaf(V.y, V.y, V.z * V.z)) >= 0.0f) return 1.0f;
+  return theta_star_general(U0, D, b.lo, b.hi, b.kk);
 }
 
 __device__ __forceinline__ bool is_boundary(int i, int j, int nx, int ny) {
@@ -230,7 +239,7 @@ __device__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t phase) {
 // relaxed density bounds, in c's own frame, and the four boosted upwind
 // Maxwellians B_vc M_k(u_upwind) (Eqs. (maxwellians12), (maxwellians34)).
 __device__ __forceinline__ void node_p2(const float4 Pc, const float4 PW, const float4 PE, const float4 PS,
-                                        const float4 PN, const Ctx& k, float4& U, float2& B, float4& M1, float4& M2,
+                                        const float4 PN, const Ctx& k, float4& U, Bnd& B, float4& M1, float4& M2,
                                         float4& M3, float4& M4) {
   const float w1 = Pc.y, w2 = Pc.z;
   float d1, d2;
@@ -247,7 +256,15 @@ __device__ __forceinline__ void node_p2(const float4 Pc, const float4 PW, const 
   const float lo = fminf(fminf(Pc.x, fminf(PW.x, PE.x)), fminf(fminf(PS.x, PN.x), U.x));
   const float hi = fmaxf(fmaxf(Pc.x, fmaxf(PW.x, PE.x)), fmaxf(fmaxf(PS.x, PN.x), U.x));
   const float delta = fmaf(k.rel, hi - lo, k.absb);
-  B = make_float2(lo - delta, hi + delta);
+  // limits of theta_star at this node: density floor max(eps_rho, lo - delta)
+  // with eps_rho = min(rho_LF, max(eps_pos, 1e-5 rho_LF)), ceiling hi + delta,
+  // and kk = eps_p / (gamma - 1) with eps_p = min(p_LF, max(eps_pos, 1e-5 p_LF))
+  const float er = fminf(U.x, fmaxf(k.eps, 1e-5f * U.x));
+  const float pLF = k.gm1 * fmaf(-0.5f, __fdividef(fmaf(U.y, U.y, U.z * U.z), U.x), U.w);
+  const float ep = fminf(pLF, fmaxf(k.eps, 1e-5f * pLF));
+  B.lo = fmaxf(er, lo - delta);
+  B.hi = hi + delta;
+  B.kk = ep * k.rg;
 }
 
 // The exact a_{n-1} -> a_n change of a rest-frame non-equilibrium part:
@@ -266,7 +283,7 @@ __device__ __forceinline__ float4 a_change_y(const float4 g, const float4 P, flo
 // theta_f of face (L, R) and theta_f d_f in L's and R's frames; gL, gR are the
 // face's outgoing part of L and incoming part of R, already at a_n.
 __device__ __forceinline__ float face_theta(const float4 PL, const float4 PR, const float4 gL, const float4 gR,
-                                            const float4 UL, const float2 BL, const float4 UR, const float2 BR,
+                                            const float4 UL, const Bnd BL, const float4 UR, const Bnd BR,
                                             bool bL, bool bR, int limiter, const Ctx& k, float4& tdL, float4& tdR) {
   float th;
   float4 dL = f4(0.f, 0.f, 0.f, 0.f), dR = dL;
@@ -278,8 +295,8 @@ __device__ __forceinline__ float face_theta(const float4 PL, const float4 PR, co
     if (limiter == 1) {
       th = 1.0f;
     } else {
-      const float tL = bL ? 1.0f : theta_star(UL, scale(-4.f, dL), BL, k.eps, k.gm1, k.rg);
-      const float tR = bR ? 1.0f : theta_star(UR, scale(4.f, dR), BR, k.eps, k.gm1, k.rg);
+      const float tL = bL ? 1.0f : theta_star(UL, scale(-4.f, dL), BL);
+      const float tR = bR ? 1.0f : theta_star(UR, scale(4.f, dR), BR);
       th = fminf(tL, tR);
     }
   }
@@ -427,7 +444,7 @@ __device__ __forceinline__ void compute_tile(const Launch& L, Boxes<TY>& Bx, Wor
     if (gi < 1 || gi > nx - 2 || gj < 1 || gj > ny - 2) continue;
     const int hx = li + 1, hy = lj + 1;
     float4 U, M1, M2, M3, M4;
-    float2 B;
+    Bnd B;
     node_p2(Bx.P[hy][hx], Bx.P[hy][hx - 1], Bx.P[hy][hx + 1], Bx.P[hy - 1][hx], Bx.P[hy + 1][hx], k, U, B, M1, M2,
             M3, M4);
     W.U[lj][li] = U;
@@ -681,15 +698,29 @@ __device__ __forceinline__ float4 shfl_down4(const float4 v) {
   return f4(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1),
             __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
 }
-__device__ __forceinline__ float2 shfl_down2(const float2 v) {
-  return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
+__device__ __forceinline__ Bnd shfl_down3(const Bnd v) {
+  return Bnd{__shfl_down_sync(0xffffffffu, v.lo, 1), __shfl_down_sync(0xffffffffu, v.hi, 1),
+             __shfl_down_sync(0xffffffffu, v.kk, 1)};
 }
 
 // blockIdx.x = (strip, row chunk) over all levels, blockIdx.y = realization;
 // MINB CTAs per SM bound the registers.
-template <int MINB>
+// Asynchronous 16-byte copy global -> shared (cp.async, L2 only); with
+// valid false it writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// PF: the rows a march step reads are copied into the lane's own shared-memory
+// ring by cp.async one step ahead (no registers held while they travel);
+// otherwise they are loaded into registers at the top of the step.
+template <int MINB, bool PF>
 __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const __grid_constant__ Launch L) {
   __shared__ float4 smk[2][4][kMNW][32];
+  __shared__ float4 ring[PF ? 2 : 1][6][kMNW][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int unit = blockIdx.x, lvl = 0;
   while (lvl + 1 < L.nlevels && unit >= L.lv[lvl + 1].tile_begin) ++lvl;
@@ -745,13 +776,13 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
   float4 M1, M2, M3, M4;
   float4 Pq = ldP(ra), Pq1 = ldP(ra + 1), Fq1 = ldF(ra + 1);
   float4 Uq = z4, PEq;
-  float2 Bq = make_float2(0.f, 0.f);
+  Bnd Bq{0.f, 0.f, 0.f};
   float thS;
   float4 tdRS, g4q;
   {
     const float4 Pm2 = ldP(ra - 2), Pm = ldP(ra - 1), Fm = ldF(ra - 1), Fq = ldF(ra);
     float4 Um = z4;
-    float2 Bm = make_float2(0.f, 0.f);
+    Bnd Bm{0.f, 0.f, 0.f};
     const float4 PWm = west(Pm, Fm), PEm = east(Pm, Fm);
     if (inner(ra - 1)) node_p2(Pm, PWm, PEm, Pm2, Pq, k, Um, Bm, M1, M2, M3, M4);
     const float4 PWq = west(Pq, Fq);
@@ -772,14 +803,47 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
   }
 
   // ---- march -----------------------------------------------------------------
+  // the rows step q reads: nodal state and far column of row q + 2, parts
+  // 1..3 of row q, part 4 of row q + 1
+  auto prefetch = [&](int q) {
+    float4(&r)[6][kMNW][32] = ring[q & 1];
+    const bool v2 = q + 2 <= ny - 1;
+    cp_async16(&r[0][wid][lane], src + (size_t)(v2 ? q + 2 : 0) * nxp + cl, v2);
+    cp_async16(&r[1][wid][lane], src + (size_t)(v2 ? q + 2 : 0) * nxp + (far ? cf : cl), v2 && far);
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) cp_async16(&r[2 + kk][wid][lane], src + (size_t)(kk + 1) * plane + (size_t)q * nxp + cl, true);
+    cp_async16(&r[5][wid][lane], src + (size_t)4 * plane + (size_t)(q + 1) * nxp + cl, true);
+  };
+  if (PF) {
+    prefetch(ra);
+    cp_async_commit();
+  }
   float lam = 0.0f;
   int flags = 0;
   for (int q = ra; q <= rb; ++q) {
-    const float4 Pq2 = ldP(q + 2), Fq2 = ldF(q + 2);
-    float4 G1 = ldG(0, q), G2 = ldG(1, q), G3 = ldG(2, q), g4n = ldG(3, q + 1);
+    float4 Pq2, Fq2, G1, G2, G3, g4n;
+    if (PF) {
+      if (q < rb) prefetch(q + 1);
+      cp_async_commit();
+      cp_async_wait_prev();
+      const float4(&r)[6][kMNW][32] = ring[q & 1];
+      Pq2 = r[0][wid][lane];
+      Fq2 = r[1][wid][lane];
+      G1 = r[2][wid][lane];
+      G2 = r[3][wid][lane];
+      G3 = r[4][wid][lane];
+      g4n = r[5][wid][lane];
+    } else {
+      Pq2 = ldP(q + 2);
+      Fq2 = ldF(q + 2);
+      G1 = ldG(0, q);
+      G2 = ldG(1, q);
+      G3 = ldG(2, q);
+      g4n = ldG(3, q + 1);
+    }
     // P2 of row q + 1
     float4 U1 = z4;
-    float2 B1 = make_float2(0.f, 0.f);
+    Bnd B1{0.f, 0.f, 0.f};
     const float4 PW1 = west(Pq1, Fq1), PE1 = east(Pq1, Fq1);
     const bool bq = !colin, b1 = !inner(q + 1);
     if (!b1) {
@@ -800,7 +864,7 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
     const float thN = face_theta(Pq, Pq1, G3, g4n, Uq, Bq, U1, B1, bq, b1, limiter, k, tdLN, tdRN);
     // east face (R = lane + 1); the west face comes from lane - 1
     const float4 gR = shfl_down4(G2), UR = shfl_down4(Uq);
-    const float2 BR = shfl_down2(Bq);
+    const Bnd BR = shfl_down3(Bq);
     float4 tdLE, tdRE;
     const float thE = face_theta(Pq, PEq, G1, gR, Uq, Bq, UR, BR, bq, !colin_e, limiter, k, tdLE, tdRE);
     const float thW = __shfl_up_sync(0xffffffffu, thE, 1);
@@ -842,9 +906,12 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
 }
 
 // Variants: 32 x 4 tiles, 32 x 8 tiles, persistent 32 x 8 tiles, warp march
-// with 4 or 5 CTAs of 4 warps per SM.
-constexpr const char* kVariantNames[] = {"tile32x4", "tile32x8", "persistent32x8", "march30x4w", "march30x5w"};
-constexpr int kNumVariants = 5;
+// with 4 or 5 CTAs of 4 warps per SM, loading into registers or prefetching
+// into shared memory.
+constexpr const char* kVariantNames[] = {"tile32x4",   "tile32x8",     "persistent32x8",
+                                         "march30x4w", "march30x5w",   "march30pf4w",
+                                         "march30pf5w"};
+constexpr int kNumVariants = 7;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -938,7 +1005,7 @@ cudaError_t launch_persistent(Launch& L, cudaStream_t s) {
 
 // Strips of kMW columns; rows split into chunks of kMNW warps with about
 // kMarchRows rows per warp.
-template <int MINB>
+template <int MINB, bool PF>
 cudaError_t launch_march(Launch& L, cudaStream_t s) {
   int units = 0;
   for (int l = 0; l < L.nlevels; ++l) {
@@ -952,7 +1019,7 @@ cudaError_t launch_march(Launch& L, cudaStream_t s) {
     units += D.tiles_x * D.tiles_y;
   }
   L.total_tiles = units;
-  step_mixed_march_kernel<MINB><<<dim3(units, L.M), kMNW * 32, 0, s>>>(L);
+  step_mixed_march_kernel<MINB, PF><<<dim3(units, L.M), kMNW * 32, 0, s>>>(L);
   add_launches(1);
   return cudaGetLastError();
 }
@@ -973,9 +1040,13 @@ cudaError_t launch_step_mixed(const Launch& Lin, int variant, cudaStream_t s) {
     case 2:
       return launch_persistent<8>(L, s);
     case 3:
-      return launch_march<4>(L, s);
+      return launch_march<4, false>(L, s);
+    case 4:
+      return launch_march<5, false>(L, s);
+    case 5:
+      return launch_march<4, true>(L, s);
     default:
-      return launch_march<5>(L, s);
+      return launch_march<5, true>(L, s);
   }
 }
 

@@ -1,0 +1,206 @@
+"""Studies on top of the library: the measurements and experiments of the
+paper's Sec. 3-4 that are more than one bench step.
+
+    python -m paper_2605_25282_gb300.studies ladder     [--precision fp64|mixed] [--steps 200]
+    python -m paper_2605_25282_gb300.studies precision  [--nx 2560 --ny 1280 --M 64 --t 0.0035]
+    python -m paper_2605_25282_gb300.studies cauchy     [--M 64 --times 0.0005,0.001,0.002,0.0035]
+
+ladder     one realization per level of the single-realization refinement
+           ladder (400x200 ... 5060x2530), fixed steps: cell-updates/s and
+           achieved GB/s (algorithmic bytes / CUDA-event time) per level.
+precision  seed-matched ensembles in the mixed path and in the FP64 path
+           (whose update is the oracle's arithmetic) advanced to t with the
+           landing rule (Sec. 2.3): per-field pathwise errors, per-statistic
+           errors of rho, and W1 between the two ensembles along the jet axis.
+cauchy     the paper's own ladder on [0, 2.5] x [-1, 1] (500x400 ... 4000x3200,
+           Sec. 3.3) advanced together, with snapshots at the given times:
+           every level's density restricted onto the coarsest grid, the error
+           functionals of Sec. 3.4 (W_11, E_mean, E_std, E_strong) of the
+           Cauchy and the reference comparisons, and their rates (Eq. (ratefit),
+           least-squares slope in log-log).
+
+Every run prints one JSON object.  All inputs are synthetic and seeded
+(Philox4x32-10 KL inlets, seed 0, realizations 0..M-1).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+
+import numpy as np
+import torch
+
+from . import vlbm
+
+BYTES_PER_UPDATE = {"fp64": 320, "mixed": 160}
+LADDER_C2 = [(400, 200), (800, 400), (1600, 800), (3200, 1600), (5060, 2530)]
+LADDER_PAPER = [(500, 400), (1000, 800), (2000, 1600), (4000, 3200)]
+
+
+def _timed_steps(ens: vlbm.Ensemble, n: int) -> float:
+    """Seconds of device time for n steps of every level, on the ensemble's stream."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(ens.stream):
+        a.record(ens.stream)
+        ens.step(n)
+        b.record(ens.stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def ladder(precision: str = "fp64", steps: int = 200, warmup: int = 4, levels=LADDER_C2, M: int = 1,
+           peak_gbs: float | None = None) -> dict:
+    out = {"study": "refinement ladder, one realization per level", "precision": precision, "M": M,
+           "steps": steps, "levels": []}
+    for nx, ny in levels:
+        ens = vlbm.Ensemble([(nx, ny)], precision=precision)
+        ens.init(0, M)
+        ens.step(warmup)
+        sec = _timed_steps(ens, steps)
+        cells = nx * ny * M * steps
+        gbs = cells * BYTES_PER_UPDATE[precision] / sec / 1e9
+        row = {"nx": nx, "ny": ny, "GLUPS": cells / sec / 1e9, "GBs": gbs, "ms_per_step": sec * 1e3 / steps,
+               "state_MB": 2 * nx * ny * M * BYTES_PER_UPDATE[precision] / 2 / 1e6}
+        if peak_gbs:
+            row["hbm_frac"] = gbs / peak_gbs
+        # levels whose state fits in L2 (129 MB) are not HBM measurements
+        row["l2_resident"] = row["state_MB"] * 2 < 129
+        out["levels"].append(row)
+        ens.sync()
+        ens.close()
+    return out
+
+
+def _rel_l1(a: torch.Tensor, b: torch.Tensor, dims) -> torch.Tensor:
+    return (a - b).abs().sum(dims) / b.abs().sum(dims)
+
+
+def precision_study(nx: int = 2560, ny: int = 1280, M: int = 64, t: float = 0.0035) -> dict:
+    ens = {p: vlbm.Ensemble([(nx, ny)], precision=p) for p in ("mixed", "fp64")}
+    secs = {}
+    for p, e in ens.items():
+        e.init(0, M)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(e.stream):
+            a.record(e.stream)
+            e.advance_to(t)
+            b.record(e.stream)
+        b.synchronize()
+        secs[p] = a.elapsed_time(b) / 1e3
+    steps = {p: e.time(0)[1] for p, e in ens.items()}
+    mo = {p: e.moments(0) for p, e in ens.items()}
+    out = {"study": "precision: mixed vs FP64, seed-matched", "nx": nx, "ny": ny, "M": M, "t": t,
+           "steps": {p: [int(s.min()), int(s.max())] for p, s in steps.items()},
+           "seconds": secs,
+           "cell_updates_per_s": {p: float(nx * ny * steps[p].sum() / secs[p]) for p in secs},
+           "pathwise_rel_l1": {}, "statistics_rel_l1": {}}
+    # per field: realization-wise relative L1 error (median and max over m)
+    for f in ("rho", "u", "v", "p"):
+        a, b = mo["mixed"][f], mo["fp64"][f]
+        if f in ("u", "v"):
+            # velocities relative to the speed scale |v1| + |v2| of the FP64 field
+            scale = (mo["fp64"]["u"].abs() + mo["fp64"]["v"].abs()).sum((1, 2))
+            e = (a - b).abs().sum((1, 2)) / scale
+        else:
+            e = _rel_l1(a, b, (1, 2))
+        out["pathwise_rel_l1"][f] = {"median": float(e.median()), "max": float(e.max())}
+    # statistics of rho (and of each field's mean) over the ensemble
+    for f in ("rho", "p"):
+        st = vlbm.stats_w1_mean_std(mo["mixed"][f], mo["fp64"][f])
+        out["statistics_rel_l1"][f] = {
+            "mean": float((st["mean_a"] - st["mean_b"]).abs().sum() / st["mean_b"].abs().sum()),
+            "std": float((st["std_a"] - st["std_b"]).abs().sum() / st["std_b"].abs().sum()),
+            "w1_over_mean": float(st["w1"].sum() / st["mean_b"].abs().sum()),
+        }
+        if f == "rho":
+            axis = st["w1"][ny // 2 - 1: ny // 2 + 1].mean(0)
+            out["w1_axis_rho"] = {"x": [float(i * 2.5 / nx) for i in range(0, nx, max(1, nx // 16))],
+                                  "w1": [float(axis[i]) for i in range(0, nx, max(1, nx // 16))],
+                                  "mean_over_axis": float(axis.mean())}
+    for e in ens.values():
+        e.close()
+    return out
+
+
+def rate(h, err) -> float | None:
+    """Least-squares slope of log err against log h (None if any err <= 0)."""
+    h, err = np.asarray(h, float), np.asarray(err, float)
+    if len(h) < 2 or np.any(err <= 0):
+        return None
+    return float(np.polyfit(np.log(h), np.log(err), 1)[0])
+
+
+def _functionals(a: torch.Tensor, b: torch.Tensor, stream) -> dict:
+    f = vlbm.stats_error_functionals(a, b, stream=stream)
+    e_mean, e_std, w11, e_strong = (float(x) for x in f.cpu())
+    return {"W_11": w11, "E_mean": e_mean, "E_std": e_std, "E_strong": e_strong}
+
+
+def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPER, precision: str = "mixed") -> dict:
+    """The paper's protocol (Sec. 3.3-3.4): every level's density restricted
+    onto the coarsest grid, the Cauchy comparison of successive levels and the
+    reference comparison against the finest, rates by Eq. (ratefit)."""
+    ens = vlbm.Ensemble(levels, precision=precision)
+    ens.init(0, M)
+    nx0, ny0 = levels[0]
+    out = {"study": "Cauchy and reference convergence on the paper's ladder", "domain": "[0, 2.5] x [-1, 1]",
+           "M": M, "precision": precision, "levels": [list(lv) for lv in levels],
+           "common_grid": [nx0, ny0], "snapshots": []}
+    keys = ("W_11", "E_mean", "E_std", "E_strong")
+    for t in times:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(ens.stream):
+            a.record(ens.stream)
+            ens.advance_to(t)
+            b.record(ens.stream)
+        b.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        steps = [ens.time(l)[1] for l in range(len(levels))]
+        common = []
+        for l, (nx, ny) in enumerate(levels):
+            d = ens.density(l, f32=False)
+            common.append(vlbm.stats_restrict(d, nx // nx0, stream=ens.stream) if nx != nx0 else d)
+            del d
+        snap = {"t": t, "seconds": sec, "steps": [[int(s.min()), int(s.max())] for s in steps],
+                "cauchy": [], "reference": []}
+        L = len(levels) - 1
+        for l in range(1, L + 1):
+            snap["cauchy"].append({"pair": [levels[l - 1][0], levels[l][0]], **_functionals(common[l - 1], common[l], ens.stream)})
+        for l in range(L):
+            snap["reference"].append({"pair": [levels[l][0], levels[L][0]], **_functionals(common[l], common[L], ens.stream)})
+        dx = [2.5 / nx for nx, _ in levels]
+        snap["rates"] = {
+            "cauchy": {k: rate(dx[:L], [p[k] for p in snap["cauchy"]]) for k in keys},
+            "reference": {k: rate(dx[:L], [p[k] for p in snap["reference"]]) for k in keys},
+        }
+        out["snapshots"].append(snap)
+        del common
+    ens.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("study", choices=["ladder", "precision", "cauchy"])
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--M", type=int, default=None)
+    ap.add_argument("--nx", type=int, default=2560)
+    ap.add_argument("--ny", type=int, default=1280)
+    ap.add_argument("--t", type=float, default=0.0035, help="final time (precision study)")
+    ap.add_argument("--times", type=str, default="0.0005,0.001,0.002,0.0035", help="snapshot times (cauchy)")
+    ap.add_argument("--peak-gbs", type=float, default=None)
+    args = ap.parse_args(argv)
+    if args.study == "ladder":
+        res = ladder(args.precision or "fp64", args.steps, M=args.M or 1, peak_gbs=args.peak_gbs)
+    elif args.study == "precision":
+        res = precision_study(args.nx, args.ny, args.M or 64, args.t)
+    else:
+        res = cauchy(args.M or 64, [float(x) for x in args.times.split(",")], precision=args.precision or "mixed")
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -31,7 +31,7 @@ EXPORTED = [
     "vlbm_init_ensemble_block", "vlbm_init_ensemble_samples", "vlbm_kernel_launches", "vlbm_step",
     "vlbm_advance_to", "vlbm_moments", "vlbm_density", "vlbm_time", "vlbm_sync", "vlbm_get_state",
     "vlbm_set_state", "stats_w1_mean_std", "stats_error_functionals", "stats_error_functionals_noalloc",
-    "stats_quantiles", "stats_histogram",
+    "stats_quantiles", "stats_histogram", "stats_restrict",
     "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_step_design", "vlbm_destroy",
 ]
 
@@ -104,6 +104,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "stats_error_functionals_noalloc": ([p, i, i, i, p, i, i, i, i, p, p], i),
         "stats_quantiles": ([p, i, i, i, i, p, i, p, p], i),
         "stats_histogram": ([p, i, i, i, i, p, i, p, p], i),
+        "stats_restrict": ([p, i, i, i, i, i, p, i, p], i),
         "vlbm_save": ([p, p, ctypes.POINTER(ctypes.c_size_t)], i),
         "vlbm_load": ([p, p, ctypes.c_size_t], i),
         "vlbm_last_error": ([p], ctypes.c_char_p),
@@ -371,6 +372,21 @@ def stats_w1_mean_std(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cu
                                  int(ens_b.dtype == torch.float32), nxb, nyb, M, *[_ptr(o) for o in out],
                                  ctypes.c_void_p(s.cuda_stream)))
     return dict(zip(("mean_a", "std_a", "mean_b", "std_b", "w1"), out))
+
+
+def stats_restrict(ens: torch.Tensor, r: int, f32: bool = False, stream: torch.cuda.Stream | None = None):
+    """Block average of every field of ens [M, ny, nx] onto [M, ny / r, nx / r] (Sec. 3.3)."""
+    _require_cuda()
+    lib = load_library()
+    if ens.dim() != 3:
+        raise ValueError("ens must be [M, ny, nx]")
+    ens = ens.contiguous()
+    M, ny, nx = ens.shape
+    out = torch.empty((M, ny // r, nx // r), dtype=torch.float32 if f32 else torch.float64, device=ens.device)
+    s = stream if stream is not None else torch.cuda.current_stream(ens.device)
+    _check(lib.stats_restrict(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, r, _ptr(out), int(f32),
+                              ctypes.c_void_p(s.cuda_stream)))
+    return out
 
 
 def stats_error_functionals(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cuda.Stream | None = None):

@@ -57,3 +57,46 @@ def test_stats_identical_ensembles_and_shift():
     assert np.all(got["w1"] == 0) and np.array_equal(got["mean_a"], got["mean_b"])
     got, _, _ = run(a, a + 0.5)
     assert np.allclose(got["w1"], 0.5, rtol=1e-12)
+
+
+@pytest.mark.parametrize("r, f32_in, f32_out", [(1, False, False), (2, True, False), (8, False, True), (5, True, True)])
+def test_restrict_matches_oracle(r, f32_in, f32_out):
+    # the restriction operator R of Sec. 3.3 (block average, same summation order)
+    M, nyc, nxc = 3, 7, 11
+    rng = np.random.default_rng(r)
+    fine = rng.lognormal(0.0, 0.5, (M, nyc * r, nxc * r))
+    if f32_in:
+        fine = fine.astype(np.float32)
+    got = vlbm.stats_restrict(torch.from_numpy(fine).cuda(), r, f32=f32_out)
+    want = O.restrict(fine.astype(np.float64), r)
+    if f32_out:
+        assert np.array_equal(got.cpu().numpy(), want.astype(np.float32))
+    else:
+        assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_sharded_statistics_single_process_equal_direct():
+    # the multi-process statistics path on one NCCL rank equals the direct call
+    import os
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_2605_25282_gb300 import sharded
+
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        rng = np.random.default_rng(5)
+        a = torch.from_numpy(rng.lognormal(0, 0.3, (9, 10, 12)).astype(np.float32)).cuda()
+        b = torch.from_numpy(rng.lognormal(0, 0.3, (9, 20, 24)).astype(np.float32)).cuda()
+        got = sharded.gpu_statistics(a, b)
+        want = vlbm.stats_w1_mean_std(a, b)
+        for k in want:
+            assert torch.equal(got[k], want[k]), k
+    finally:
+        dist.destroy_process_group()
