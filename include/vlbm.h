@@ -199,6 +199,23 @@ int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const v
                       int b_is_f32, int nxb, int nyb, int M, double* mean_a, double* std_a,
                       double* mean_b, double* std_b, double* w1, void* cuda_stream);
 
+/* Sec. 3.4, Eq. (w2): the two-point Wasserstein distance W_{1,2} between
+ * ensemble a [M][nya][nxa] and ensemble b [M][nyb][nxb] (device pointers;
+ * FP32 when *_is_f32 != 0, else FP64), b block-restricted onto a's grid
+ * (nxb = r nxa, nyb = r nya).  The grid is subsampled to npd x npd points,
+ * x_k = the centre cell (((2 kx + 1) nxa) / (2 npd), ((2 ky + 1) nya) / (2 npd))
+ * of each of npd equal strips per direction, k = ky npd + kx; for every
+ * ordered pair (k, k'), the first Wasserstein distance on R^2 (Euclidean
+ * cost) between the empirical joint laws of (rho(x_k), rho(x_k')) of the two
+ * ensembles is computed exactly (optimal assignment of the M points, FP64).
+ * *w12 (device) receives the mean over the P = npd^4 pairs; pairs (device
+ * [P], pair k npd^2 + k', may be NULL: scratch then comes from the
+ * stream-ordered allocator) the per-pair values.  1 <= M <= 2048,
+ * 1 <= npd <= min(nxa, nya, 215).  Asynchronous on cuda_stream (may be NULL);
+ * results are reproducible bit for bit. */
+int stats_w1_two_point(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32, int nxb,
+                       int nyb, int M, int npd, double* w12, double* pairs, void* cuda_stream);
+
 /* Sec. 3.3: the conservative restriction operator R, block averaging of each
  * of the M fields ens [M][ny][nx] (device; FP32 when is_f32 != 0, else FP64)
  * onto the coarse grid [M][ny/r][nx/r]: coarse cell (I, J) is the mean of
@@ -272,6 +289,39 @@ const char* vlbm_last_error(const vlbm_ctx* ctx);
  * (graph replays count every kernel node).  Instrumentation for benchmarks. */
 unsigned long long vlbm_kernel_launches(void);
 
+/* Gradient of an ensemble observable with respect to the per-mode amplitudes
+ * a_1..a_K of the KL inlet perturbation (Sec. 2.3, Eq. (karhunenExp)): the
+ * hand-written discrete adjoint of the FP64 step (Eqs. (vlbm1)-(vlbm5), the
+ * R-theta limiter, the boundaries of Sec. 2.2 and the kinetic speed of
+ * Sec. 2.1).  From the initial state of the context's last initialisation
+ * (re-created here), the context advances nsteps fixed FP64 steps, keeping a
+ * checkpoint every checkpoint_every steps; then the reverse sweep restores
+ * each checkpoint, recomputes the states of its window and runs the adjoint
+ * step backwards through them.  The observable is
+ *   J = (1/M) sum_m sum_{i,j} w[j][i] rho_m(i, j, t_nsteps),
+ * w a device array [ny][nx] (the axial ensemble-mean density is w = 1/2 on
+ * the two rows next to y = 0, times the weight of each column).  On return
+ * grad_out[k - 1] = dJ/da_k (host, K doubles, K of the last initialisation)
+ * and, if J_out is not NULL, *J_out = J; the context is left at step nsteps.
+ * The discrete map is piecewise smooth: the argmax of lambda, the limiter's
+ * minima and branches are differentiated on the branch the forward step
+ * takes.  Realizations of the jet diverge pathwise (Sec. 4: the strong error
+ * does not converge), so such a gradient describes the ensemble only over
+ * windows shorter than the divergence time.  Needs an FP64 single-level
+ * context; device memory for ceil(nsteps / checkpoint_every) + checkpoint_every
+ * + 4 states plus ~90 FP64 planes per realization comes from the context's
+ * allocator and is released before return.  Synchronises the stream.
+ * Returns VLBM_EINVAL (wrong context or arguments), VLBM_ENOMEM, VLBM_ECUDA,
+ * or the positivity / finiteness status of the forward run.  No counterpart
+ * in the paper, which computes no gradients. */
+int vlbm_grad_amplitudes(vlbm_ctx* ctx, int nsteps, int checkpoint_every, const double* w, double* J_out,
+                         double* grad_out);
+
+/* The per-mode amplitudes of the context's last initialisation: *K (may be
+ * NULL) receives their number, amp (host, may be NULL) the values
+ * (A k^-p unless overridden).  VLBM_EINVAL for a NULL ctx. */
+int vlbm_amplitudes(const vlbm_ctx* ctx, double* amp, int* K);
+
 /* The launch design the mixed-precision step kernel runs with in ctx: its
  * index, its name (static storage) and the number of designs.  The designs
  * (tile shapes, persistent CTAs, warps marching up column strips) compute
@@ -282,6 +332,15 @@ unsigned long long vlbm_kernel_launches(void);
  * whose update has a single implementation.  Returns VLBM_EINVAL for a NULL
  * ctx. */
 int vlbm_step_design(const vlbm_ctx* ctx, int* index, const char** name, int* count);
+
+/* Failure-detection check of the device waits: runs on the current device
+ * one mbarrier wait that nothing completes, bounded by limit_s seconds
+ * (0 < limit_s <= 10) as every wait of the step kernels is bounded, and
+ * reports how it ended.  Returns VLBM_ETIMEOUT when the bound ended the wait
+ * (the designed outcome: the kernel returned, nothing is in flight, the
+ * context stays usable), VLBM_ECUDA otherwise, VLBM_EINVAL for a bad limit.
+ * Synchronous.  No counterpart in the paper. */
+int vlbm_check_bounded_wait(double limit_s);
 
 /* Frees the context and everything it allocated.  Accepts NULL. */
 void vlbm_destroy(vlbm_ctx* ctx);

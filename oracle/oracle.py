@@ -338,6 +338,51 @@ def error_functionals(ens_a: np.ndarray, ens_b: np.ndarray):
     return e_mean, e_std, w11, strong / M
 
 
+def w1_points_2d(a: np.ndarray, b: np.ndarray) -> float:
+    """First Wasserstein distance between the uniform empirical measures of the
+    M points a [M, 2] and b [M, 2] on R^2 with Euclidean ground cost: the
+    optimal assignment (scipy's linear_sum_assignment on the cost matrix),
+    (1/M) min over permutations sigma of sum_i |a_i - b_sigma(i)|."""
+    from scipy.optimize import linear_sum_assignment
+
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    dx = a[:, None, 0] - b[None, :, 0]
+    dy = a[:, None, 1] - b[None, :, 1]
+    C = np.sqrt(dx * dx + dy * dy)
+    r, c = linear_sum_assignment(C)
+    return float(C[r, c].sum() / a.shape[0])
+
+
+def two_point_points(nx: int, ny: int, npd: int):
+    """The npd x npd subsample of a grid: the centre cell of each of npd equal
+    strips per direction, as (i, j) in row-major order (j outer)."""
+    xs = [((2 * k + 1) * nx) // (2 * npd) for k in range(npd)]
+    ys = [((2 * k + 1) * ny) // (2 * npd) for k in range(npd)]
+    return [(i, j) for j in ys for i in xs]
+
+
+def w1_two_point(ens_a: np.ndarray, ens_b: np.ndarray, npd: int = 10):
+    """Two-point Wasserstein distance W_{1,2} (Sec. 3.4, Eq. (w2)) between a
+    coarse ensemble [M, ny, nx] and a fine one [M, r ny, r nx] restricted onto
+    it: for every ordered pair (x_k, x_k') of the npd x npd subsample, the W1
+    on R^2 between the empirical joint laws of (rho(x_k), rho(x_k')) of the two
+    ensembles; returns (the mean over the P = npd^4 pairs, the per-pair values
+    in pair order k * npd^2 + k')."""
+    ens_a = np.asarray(ens_a, dtype=np.float64)
+    r = ens_b.shape[-1] // ens_a.shape[-1]
+    b = restrict(ens_b, r) if r > 1 else np.asarray(ens_b, dtype=np.float64)
+    M, ny, nx = ens_a.shape
+    pts = two_point_points(nx, ny, npd)
+    out = np.zeros(len(pts) * len(pts))
+    for k, (i, j) in enumerate(pts):
+        for k2, (i2, j2) in enumerate(pts):
+            A = np.stack([ens_a[:, j, i], ens_a[:, j2, i2]], 1)
+            B = np.stack([b[:, j, i], b[:, j2, i2]], 1)
+            out[k * len(pts) + k2] = w1_points_2d(A, B)
+    return float(out.mean()), out
+
+
 def quantile(samples: np.ndarray, alpha: float) -> np.ndarray:
     """Empirical alpha-quantile per cell, Eq. (empcdf):
     p_alpha = inf{xi : F(xi) >= alpha} = the ceil(alpha M)-th smallest sample."""

@@ -19,13 +19,14 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvlbm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["vlbm_api.cu", "vlbm_aux.cu", "vlbm_diag.cu", "vlbm_stats.cu", "vlbm_step_f64.cu", "vlbm_step_mixed.cu"]
+SOURCES = ["vlbm_adjoint.cu", "vlbm_api.cu", "vlbm_aux.cu", "vlbm_diag.cu", "vlbm_stats.cu", "vlbm_step_f64.cu",
+           "vlbm_step_mixed.cu", "vlbm_w12.cu"]
 # No implicit FMA contraction: the FP64 path evaluates every expression in the
 # oracle's order with separate roundings, so it agrees with the oracle to
 # round-off; the mixed path spells out each fused multiply-add, so every tile
 # shape and launch design computes bit-identical results.
 PER_FILE = {"vlbm_step_f64.cu": ["-fmad=false"], "vlbm_aux.cu": ["-fmad=false"],
-            "vlbm_step_mixed.cu": ["-fmad=false"]}
+            "vlbm_step_mixed.cu": ["-fmad=false"], "vlbm_adjoint.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE]
 
@@ -39,7 +40,8 @@ def nvcc() -> str:
 
 def _deps() -> list[str]:
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "vlbm_internal.cuh"), os.path.join(INCLUDE, "vlbm.h")]
+    files += [os.path.join(CSRC, "vlbm_internal.cuh"), os.path.join(CSRC, "vlbm_f64_math.cuh"),
+              os.path.join(INCLUDE, "vlbm.h")]
     return files
 
 

@@ -6,6 +6,7 @@
 //   tick kernel  (per realization: t, step count, lambda -> a_{n+1}, landing)
 // vlbm_step / vlbm_advance_to replay a captured graph of kGraphSteps such
 // pairs, so a long run costs one graph launch per kGraphSteps steps.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -78,8 +79,10 @@ struct vlbm_ctx {
   std::vector<LevelMem> mem;
   Launch launch{};
   int* d_count = nullptr;
-  double* d_xi = nullptr;  // given KL uniforms (vlbm_init_ensemble_samples)
+  double* d_xi = nullptr;  // KL uniforms of every realization, given or drawn: [M][2K]
   size_t xi_bytes = 0;
+  std::vector<double> amp;  // per-mode amplitudes of the last initialisation
+  double r_jet = 0.05;
   cudaGraphExec_t graph = nullptr;
   bool warmed = false;
   int variant = -1;  // mixed kernel launch design (index), -1: not tuned yet
@@ -394,22 +397,26 @@ int init_impl(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb
     add_launches(1);
     if (e != cudaSuccess) return cuda_fail(c, e, "clearing the lattice");
   }
+  // the KL uniforms are kept (given, or recorded when drawn) for gradients
+  const size_t xi_bytes = (size_t)M * 2 * P.K * sizeof(double);
+  if (xi_bytes > c->xi_bytes) {
+    dev_free(c, c->d_xi);
+    c->d_xi = static_cast<double*>(dev_alloc(c, xi_bytes));
+    c->xi_bytes = c->d_xi ? xi_bytes : 0;
+    if (!c->d_xi) return fail(c, VLBM_ENOMEM, "device allocation of the KL uniforms failed");
+  }
   const double* d_xi = nullptr;
   if (xi) {
-    const size_t bytes = (size_t)M * 2 * P.K * sizeof(double);
-    if (bytes > c->xi_bytes) {
-      dev_free(c, c->d_xi);
-      c->d_xi = static_cast<double*>(dev_alloc(c, bytes));
-      c->xi_bytes = c->d_xi ? bytes : 0;
-      if (!c->d_xi) return fail(c, VLBM_ENOMEM, "device allocation of the KL uniforms failed");
-    }
-    if (bytes) {
-      e = cudaMemcpyAsync(c->d_xi, xi, bytes, cudaMemcpyDefault, c->stream);
+    if (xi_bytes) {
+      e = cudaMemcpyAsync(c->d_xi, xi, xi_bytes, cudaMemcpyDefault, c->stream);
       if (e != cudaSuccess) return cuda_fail(c, e, "copying the KL uniforms");
     }
     d_xi = c->d_xi;
   }
-  e = launch_inlet(L, seed, m_begin, P, d_xi, c->stream);
+  c->amp.assign(P.K, 0.0);
+  for (int k = 1; k <= P.K; ++k) c->amp[k - 1] = P.use_amp ? P.amp[k - 1] : P.A * std::pow((double)k, -P.p_decay);
+  c->r_jet = P.r_jet;
+  e = launch_inlet(L, seed, m_begin, P, d_xi, c->d_xi, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "inlet kernel");
   e = launch_init_state(L, c->precision, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "initial state kernel");
@@ -638,6 +645,30 @@ int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const v
   return VLBM_OK;
 }
 
+int stats_w1_two_point(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32, int nxb,
+                       int nyb, int M, int npd, double* w12, double* pairs, void* cuda_stream) {
+  if (!ens_a || !ens_b || !w12) return fail(nullptr, VLBM_EINVAL, "ensemble and output pointers must be non-NULL");
+  if (nxa < 1 || nya < 1 || nxb < nxa || nxb % nxa || nyb != nya * (nxb / nxa))
+    return fail(nullptr, VLBM_EINVAL, "ensemble b must be an integer refinement of ensemble a");
+  if (M < 1 || M > 2048) return fail(nullptr, VLBM_EINVAL, "M must be in [1, 2048]");
+  if (npd < 1 || npd > nxa || npd > nya || npd > 215)
+    return fail(nullptr, VLBM_EINVAL, "npd must be in [1, min(nx, ny, 215)]");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const size_t P = (size_t)npd * npd * npd * npd;
+  double* scratch = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!pairs) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), P * sizeof(double), s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMallocAsync for the pair values");
+  }
+  e = w12_launch(ens_a, a_is_f32 != 0, nxa, nya, ens_b, b_is_f32 != 0, nxb, nxb / nxa, M, npd, pairs ? pairs : scratch,
+                 w12, s);
+  cudaError_t e2 = scratch ? cudaFreeAsync(scratch, s) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "two-point Wasserstein kernels");
+  if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "cudaFreeAsync");
+  return VLBM_OK;
+}
+
 int stats_restrict(const void* ens, int is_f32, int nx, int ny, int M, int r, void* out, int out_is_f32,
                    void* cuda_stream) {
   if (!ens || !out) return fail(nullptr, VLBM_EINVAL, "ensemble and output pointers must be non-NULL");
@@ -755,6 +786,153 @@ int vlbm_load(vlbm_ctx* c, const void* host_buf, size_t bytes) {
   }
   c->prepared = false;
   return VLBM_OK;
+}
+
+int vlbm_grad_amplitudes(vlbm_ctx* c, int nsteps, int checkpoint_every, const double* w, double* J_out,
+                         double* grad_out) {
+  if (!c) return fail(nullptr, VLBM_EINVAL, "ctx is NULL");
+  if (!c->initialized) return fail(c, VLBM_ESTATE, "vlbm_init_ensemble has not been called");
+  if (c->precision != VLBM_FP64) return fail(c, VLBM_EINVAL, "gradients need an FP64 context");
+  if (c->grids.size() != 1) return fail(c, VLBM_EINVAL, "gradients need a single-level context");
+  if (nsteps < 0 || checkpoint_every < 1) return fail(c, VLBM_EINVAL, "need nsteps >= 0 and checkpoint_every >= 1");
+  if (!w || !grad_out) return fail(c, VLBM_EINVAL, "w and grad_out are required");
+  const int K = (int)c->amp.size();
+  const int M = c->M;
+  const Launch& L = c->launch;
+  const LevelDesc& D = L.lv[0];
+  cudaStream_t st = c->stream;
+  const size_t sdoubles = (size_t)M * D.real_stride;  // one lattice of every realization
+  const size_t sbytes = sdoubles * sizeof(double), rbytes = (size_t)M * sizeof(RealState);
+  const int ncp = nsteps == 0 ? 0 : (nsteps + checkpoint_every - 1) / checkpoint_every;
+  const int wlen = nsteps < checkpoint_every ? (nsteps > 0 ? nsteps : 1) : checkpoint_every;
+  // device buffers (the context's allocator), released on every exit
+  std::vector<void*> owned;
+  bool alloc_failed = false;
+  auto get = [&](size_t bytes) -> void* {
+    void* p = dev_alloc(c, bytes ? bytes : 16);
+    if (p)
+      owned.push_back(p);
+    else
+      alloc_failed = true;
+    return p;
+  };
+  auto release = [&]() {
+    for (void* p : owned) dev_free(c, p);
+    owned.clear();
+  };
+  double* ck = static_cast<double*>(get(sbytes * (size_t)(ncp > 0 ? ncp : 1)));
+  RealState* ckr = static_cast<RealState*>(get(rbytes * (size_t)(ncp > 0 ? ncp : 1)));
+  double* tr = static_cast<double*>(get(sbytes * (size_t)wlen));
+  RealState* trr = static_cast<RealState*>(get(rbytes * (size_t)wlen));
+  double* fin = static_cast<double*>(get(sbytes));
+  RealState* finr = static_cast<RealState*>(get(rbytes));
+  double* adj = static_cast<double*>(get(2 * sbytes));
+  double* scr = static_cast<double*>(get(adjoint_scratch_doubles(D, M) * sizeof(double)));
+  int* iscr = static_cast<int*>(get(adjoint_scratch_ints(D, M) * sizeof(int)));
+  double* inl = static_cast<double*>(get((size_t)M * D.ny * sizeof(double)));
+  double* Jm = static_cast<double*>(get((size_t)M * sizeof(double)));
+  double* gd = static_cast<double*>(get((size_t)(K > 0 ? K : 1) * sizeof(double)));
+  if (alloc_failed) {
+    release();
+    return fail(c, VLBM_ENOMEM, "device allocation for the adjoint failed");
+  }
+  double* lat = static_cast<double*>(D.lat);
+  auto parity_ptr = [&](long long s) { return lat + (size_t)(s & 1) * sdoubles; };
+  cudaError_t e = cudaSuccess;
+  auto save = [&](long long s, double* dst, RealState* dr) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, parity_ptr(s), sbytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dr, D.rs, rbytes, cudaMemcpyDeviceToDevice, st);
+  };
+  auto restore = [&](long long s, const double* src, const RealState* sr) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(parity_ptr(s), src, sbytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D.rs, sr, rbytes, cudaMemcpyDeviceToDevice, st);
+  };
+  // 1. back to the initial state (the inlet data persist) and forward with checkpoints
+  e = launch_init_state(L, c->precision, st);
+  if (e == cudaSuccess) e = launch_lambda(L, c->precision, 0, 0, M, st);
+  if (e == cudaSuccess) e = launch_fill_equilibrium_f64(L, 0, 0, M, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(inl, 0, (size_t)M * D.ny * sizeof(double), st);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "resetting the initial state");
+  }
+  c->prepared = false;
+  int stt = prepare(c, std::numeric_limits<double>::infinity());
+  for (long long s = 0; s < nsteps && stt == VLBM_OK && e == cudaSuccess; ++s) {
+    if (s % checkpoint_every == 0) save(s, ck + (size_t)(s / checkpoint_every) * sdoubles, ckr + (s / checkpoint_every) * M);
+    stt = launch_one_step(c);
+  }
+  save(nsteps, fin, finr);
+  if (stt == VLBM_OK && e == cudaSuccess) stt = read_flags(c, -1, nullptr);
+  if (stt != VLBM_OK || e != cudaSuccess) {
+    release();
+    return stt != VLBM_OK ? stt : cuda_fail(c, e, "forward sweep");
+  }
+  // 2. J and the seed; 3. reverse sweep window by window
+  int cur = 0;
+  double* A[2] = {adj, adj + sdoubles};
+  e = adjoint_objective(L, 0, fin, w, Jm, A[cur], st);
+  for (int wi = ncp - 1; wi >= 0 && e == cudaSuccess && stt == VLBM_OK; --wi) {
+    const long long s0 = (long long)wi * checkpoint_every;
+    const long long s1 = std::min<long long>(s0 + checkpoint_every, nsteps);
+    restore(s0, ck + (size_t)wi * sdoubles, ckr + (size_t)wi * M);
+    for (long long s = s0; s < s1 && e == cudaSuccess && stt == VLBM_OK; ++s) {
+      save(s, tr + (size_t)(s - s0) * sdoubles, trr + (size_t)(s - s0) * M);
+      if (s + 1 < s1) stt = launch_one_step(c);
+    }
+    for (long long s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
+      e = adjoint_step(L, 0, c->r_jet, tr + (size_t)(s - s0) * sdoubles, trr + (size_t)(s - s0) * M, A[cur],
+                       A[cur ^ 1], scr, iscr, inl, st);
+      cur ^= 1;
+    }
+  }
+  // 4. the initial state and the amplitudes
+  if (e == cudaSuccess && stt == VLBM_OK) {
+    const double* s0 = nsteps > 0 ? tr : fin;
+    const RealState* r0 = nsteps > 0 ? trr : finr;
+    e = adjoint_initial(L, 0, c->r_jet, s0, r0, A[cur], A[cur ^ 1], scr, inl, st);
+  }
+  if (e == cudaSuccess && stt == VLBM_OK && K > 0) e = adjoint_amplitudes(L, 0, c->r_jet, inl, c->d_xi, K, gd, st);
+  // 5. the context is left at step nsteps of the forward run
+  restore(nsteps, fin, finr);
+  std::vector<double> hJ(M);
+  if (e == cudaSuccess && stt == VLBM_OK && K > 0)
+    e = cudaMemcpyAsync(grad_out, gd, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && stt == VLBM_OK)
+    e = cudaMemcpyAsync(hJ.data(), Jm, (size_t)M * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release();
+  if (stt != VLBM_OK) return stt;
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint sweep");
+  if (J_out) {
+    double J = 0.0;
+    for (int m = 0; m < M; ++m) J += hJ[m];
+    *J_out = J / M;
+  }
+  return VLBM_OK;
+}
+
+int vlbm_amplitudes(const vlbm_ctx* c, double* amp, int* K) {
+  if (!c) return VLBM_EINVAL;
+  if (K) *K = (int)c->amp.size();
+  if (amp)
+    for (size_t k = 0; k < c->amp.size(); ++k) amp[k] = c->amp[k];
+  return VLBM_OK;
+}
+
+int vlbm_check_bounded_wait(double limit_s) {
+  if (!(limit_s > 0.0) || limit_s > 10.0) return fail(nullptr, VLBM_EINVAL, "limit_s must be in (0, 10]");
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&d), sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc");
+  int h = -1;
+  e = cudaMemset(d, 0xff, sizeof(int));
+  if (e == cudaSuccess) e = launch_bounded_wait_probe(d, (unsigned long long)(limit_s * 1e9), nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounded wait probe");
+  if (h == 4) return fail(nullptr, VLBM_ETIMEOUT, "the bounded device wait gave up as designed");
+  return fail(nullptr, VLBM_ECUDA, "the bounded device wait returned status " + std::to_string(h));
 }
 
 unsigned long long vlbm_kernel_launches(void) { return g_launches.load(); }

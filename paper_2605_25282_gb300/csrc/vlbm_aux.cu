@@ -49,6 +49,7 @@ struct PerturbDev {
   double amp[kMaxModes];
   uint32_t key0, key1;
   const double* xi;  // [M][2K] given uniforms (Y then Z), or NULL: Philox draws
+  double* xi_out;    // [M][2K]: where the drawn uniforms are recorded (may be NULL)
 };
 
 // One thread per (level, realization, row).
@@ -76,6 +77,12 @@ __global__ void inlet_kernel(const Launch L, const PerturbDev P) {
         Y[idx] = u;
       else
         Z[idx - P.K] = u;
+    }
+  }
+  if (P.xi_out && j == 0) {
+    for (int k = 0; k < P.K; ++k) {
+      P.xi_out[(size_t)m * 2 * P.K + k] = Y[k];
+      P.xi_out[(size_t)m * 2 * P.K + P.K + k] = Z[k];
     }
   }
   const double y = __dadd_rn(D.y_min, __dmul_rn((double)j + 0.5, D.dx));
@@ -517,10 +524,50 @@ inline dim3 node_grid(const LevelDesc& D, int count) {
   return dim3((unsigned)((n + kThreads - 1) / kThreads), (unsigned)count, 1);
 }
 
+// A device wait that nothing completes, bounded like every wait of the step
+// kernels: one mbarrier expecting 16 bytes that no copy delivers.  The wait
+// gives up after limit_ns of %globaltimer, records 4 in *status (the bit the
+// step kernels raise) and the kernel returns; no copy is in flight.
+__global__ void bounded_wait_probe_kernel(int* status, unsigned long long limit_ns) {
+  __shared__ alignas(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(16) : "memory");
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(b), "r"(0)
+        : "memory");
+    if (ok) {
+      *status = 0;
+      return;
+    }
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit_ns) {
+      *status = 4;
+      return;
+    }
+  }
+}
+
 }  // namespace
 
+cudaError_t launch_bounded_wait_probe(int* status, unsigned long long limit_ns, cudaStream_t s) {
+  bounded_wait_probe_kernel<<<1, 32, 0, s>>>(status, limit_ns);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, const double* xi,
-                         cudaStream_t s) {
+                         double* xi_out, cudaStream_t s) {
   PerturbDev pd{};
   pd.xi = xi;
   pd.r_jet = P.r_jet;
@@ -533,6 +580,7 @@ cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm
     dim3 grid((L.lv[l].ny + kThreads - 1) / kThreads, L.M, 1);
     Launch one = L;
     one.lv[0] = L.lv[l];
+    pd.xi_out = (l == 0 && !xi) ? xi_out : nullptr;
     inlet_kernel<<<grid, kThreads, 0, s>>>(one, pd);
     add_launches(1);
   }

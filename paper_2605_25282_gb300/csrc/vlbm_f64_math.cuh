@@ -1,0 +1,78 @@
+// FP64 arithmetic of the paper's update shared by the FP64 step kernel and
+// its adjoint: primitive recovery (Eq. (eos)), the Euler fluxes
+// (Eqs. (fluxF), (fluxG)) and the R-theta limiter.  Both translation units are
+// compiled without FMA contraction and evaluate these in the oracle's order,
+// so the adjoint re-evaluates exactly the branches the forward step took.
+#pragma once
+
+namespace vlbm {
+namespace f64 {
+
+__device__ __forceinline__ void primitive(const double q[4], double gamma, double& v1, double& v2,
+                                          double& p) {
+  v1 = q[1] / q[0];
+  v2 = q[2] / q[0];
+  p = (gamma - 1.0) * (q[3] - 0.5 * q[0] * (v1 * v1 + v2 * v2));
+}
+
+__device__ __forceinline__ void fluxes(const double q[4], double gamma, double f[4], double g[4]) {
+  double v1, v2, p;
+  primitive(q, gamma, v1, v2, p);
+  f[0] = q[1];
+  f[1] = q[1] * v1 + p;
+  f[2] = q[1] * v2;
+  f[3] = (q[3] + p) * v1;
+  g[0] = q[2];
+  g[1] = q[1] * v2;
+  g[2] = q[2] * v2 + p;
+  g[3] = (q[3] + p) * v2;
+}
+
+// Largest theta in [0, 1] keeping U0 + theta D inside the admissible,
+// relaxed-bounded set (convex: the feasible thetas form [0, theta*]).
+static __device__ double theta_star(const double U0[4], const double D[4], double lo_b, double hi_b,
+                             double eps_r, double eps_p, double gamma) {
+  double th = 1.0;
+  const double lower = eps_r > lo_b ? eps_r : lo_b;
+  if (D[0] < 0.0) {
+    const double lim = (U0[0] - lower) / (-D[0]);
+    if (lim < th) th = lim;
+  } else if (D[0] > 0.0) {
+    const double lim = (hi_b - U0[0]) / D[0];
+    if (lim < th) th = lim;
+  }
+  if (th < 0.0) th = 0.0;
+  const double kk = eps_p / (gamma - 1.0);
+  const double C = U0[0] * U0[3] - 0.5 * (U0[1] * U0[1] + U0[2] * U0[2]) - kk * U0[0];
+  const double B = U0[0] * D[3] + D[0] * U0[3] - (U0[1] * D[1] + U0[2] * D[2]) - kk * D[0];
+  const double A = D[0] * D[3] - 0.5 * (D[1] * D[1] + D[2] * D[2]);
+  const double qth = C + th * (B + th * A);
+  if (qth >= 0.0) return th;
+  if (C <= 0.0) return 0.0;
+  double r;
+  if (A == 0.0) {
+    r = -C / B;
+  } else {
+    double disc = B * B - 4.0 * A * C;
+    if (disc < 0.0) disc = 0.0;
+    const double sq = sqrt(disc);
+    const double Q = -0.5 * (B + (B >= 0.0 ? sq : -sq));
+    if (Q == 0.0) return 0.0;
+    const double r1 = Q / A;
+    const double r2 = C / Q;
+    r = -1.0;
+    if (r1 > 0.0) r = r1;
+    if (r2 > 0.0 && (r < 0.0 || r2 < r)) r = r2;
+    if (r < 0.0) return 0.0;
+  }
+  if (r > th) r = th;
+  if (r < 0.0) r = 0.0;
+  return r;
+}
+
+__device__ __forceinline__ bool is_boundary(int i, int j, int nx, int ny) {
+  return i == 0 || i == nx - 1 || j == 0 || j == ny - 1;
+}
+
+}  // namespace f64
+}  // namespace vlbm

@@ -130,8 +130,34 @@ cudaError_t launch_step_mixed(const Launch& L, int variant, cudaStream_t s);
 cudaError_t restrict_launch(const void* ens, int is_f32, int nx, int ny, int M, int r, void* out, int out_f32,
                             cudaStream_t s);
 
+// Two-point Wasserstein distance (vlbm_w12.cu): per-pair values into pair_w
+// [npd^4] and their mean into *out (device).  Dynamic shared memory per CTA:
+size_t w12_smem_bytes(int M);
+cudaError_t w12_launch(const void* a, int a_f32, int nxa, int nya, const void* b, int b_f32, int nxb, int r, int M,
+                       int npd, double* pair_w, double* out, cudaStream_t s);
+
+// One mbarrier wait that nothing completes, bounded by limit_ns; *status = 4
+// (device int) when the bound ended it.
+cudaError_t launch_bounded_wait_probe(int* status, unsigned long long limit_ns, cudaStream_t s);
+
+// xi: NULL (Philox draws from seed, m_begin) or device [M][2K] given uniforms;
+// with Philox draws, xi_out (device [M][2K], may be NULL) receives them.
 cudaError_t launch_inlet(const Launch& L, uint64_t seed, int m_begin, const vlbm_perturb& P, const double* xi,
+                         double* xi_out, cudaStream_t s);
+
+// Discrete adjoint of the FP64 step on one level (vlbm_adjoint.cu).  States
+// are [M][20][plane] FP64 (u, populations) in the lattice layout.
+size_t adjoint_scratch_doubles(const LevelDesc& D, int M);
+size_t adjoint_scratch_ints(const LevelDesc& D, int M);
+cudaError_t adjoint_objective(const Launch& L, int level, const double* state, const double* w, double* Jm,
+                              double* aseed, cudaStream_t s);
+cudaError_t adjoint_step(const Launch& L, int level, double r_jet, const double* state, const RealState* rs,
+                         const double* ain, double* aout, double* scr, int* iscr, double* inlet_acc,
                          cudaStream_t s);
+cudaError_t adjoint_initial(const Launch& L, int level, double r_jet, const double* state0, const RealState* rs0,
+                            const double* ain, double* aout, double* scr, double* inlet_acc, cudaStream_t s);
+cudaError_t adjoint_amplitudes(const Launch& L, int level, double r_jet, const double* inlet_acc, const double* xi,
+                               int K, double* grad, cudaStream_t s);
 cudaError_t launch_init_state(const Launch& L, int precision, cudaStream_t s);
 cudaError_t launch_lambda(const Launch& L, int precision, int level, int m0, int count, cudaStream_t s);
 cudaError_t launch_fill_equilibrium_f64(const Launch& L, int level, int m0, int count, cudaStream_t s);

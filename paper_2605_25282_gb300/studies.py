@@ -11,11 +11,13 @@ ladder     one realization per level of the single-realization refinement
 precision  seed-matched ensembles in the mixed path and in the FP64 path
            (whose update is the oracle's arithmetic) advanced to t with the
            landing rule (Sec. 2.3): per-field pathwise errors, per-statistic
-           errors of rho, and W1 between the two ensembles along the jet axis.
+           errors of rho and p, and W1 between the two ensembles along the jet
+           axis; with --control, the same figures for two FP64 ensembles whose
+           amplitudes differ by 1e-7 (the jet's own pathwise divergence).
 cauchy     the paper's own ladder on [0, 2.5] x [-1, 1] (500x400 ... 4000x3200,
            Sec. 3.3) advanced together, with snapshots at the given times:
            every level's density restricted onto the coarsest grid, the error
-           functionals of Sec. 3.4 (W_11, E_mean, E_std, E_strong) of the
+           functionals of Sec. 3.4 (W_11, W_12, E_mean, E_std, E_strong) of the
            Cauchy and the reference comparisons, and their rates (Eq. (ratefit),
            least-squares slope in log-log).
 
@@ -27,7 +29,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 
 import numpy as np
 import torch
@@ -77,50 +78,69 @@ def _rel_l1(a: torch.Tensor, b: torch.Tensor, dims) -> torch.Tensor:
     return (a - b).abs().sum(dims) / b.abs().sum(dims)
 
 
-def precision_study(nx: int = 2560, ny: int = 1280, M: int = 64, t: float = 0.0035) -> dict:
-    ens = {p: vlbm.Ensemble([(nx, ny)], precision=p) for p in ("mixed", "fp64")}
-    secs = {}
-    for p, e in ens.items():
-        e.init(0, M)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(e.stream):
-            a.record(e.stream)
-            e.advance_to(t)
-            b.record(e.stream)
-        b.synchronize()
-        secs[p] = a.elapsed_time(b) / 1e3
-    steps = {p: e.time(0)[1] for p, e in ens.items()}
-    mo = {p: e.moments(0) for p, e in ens.items()}
-    out = {"study": "precision: mixed vs FP64, seed-matched", "nx": nx, "ny": ny, "M": M, "t": t,
-           "steps": {p: [int(s.min()), int(s.max())] for p, s in steps.items()},
-           "seconds": secs,
-           "cell_updates_per_s": {p: float(nx * ny * steps[p].sum() / secs[p]) for p in secs},
-           "pathwise_rel_l1": {}, "statistics_rel_l1": {}}
-    # per field: realization-wise relative L1 error (median and max over m)
+def _pathwise(a: dict, b: dict) -> dict:
+    """Realization-wise relative L1 differences of rho, u, v, p (median, max over m)."""
+    out = {}
     for f in ("rho", "u", "v", "p"):
-        a, b = mo["mixed"][f], mo["fp64"][f]
         if f in ("u", "v"):
-            # velocities relative to the speed scale |v1| + |v2| of the FP64 field
-            scale = (mo["fp64"]["u"].abs() + mo["fp64"]["v"].abs()).sum((1, 2))
-            e = (a - b).abs().sum((1, 2)) / scale
+            # velocities relative to the speed scale |v1| + |v2| of the reference field
+            scale = (b["u"].abs() + b["v"].abs()).sum((1, 2))
+            e = (a[f] - b[f]).abs().sum((1, 2)) / scale
         else:
-            e = _rel_l1(a, b, (1, 2))
-        out["pathwise_rel_l1"][f] = {"median": float(e.median()), "max": float(e.max())}
-    # statistics of rho (and of each field's mean) over the ensemble
+            e = _rel_l1(a[f], b[f], (1, 2))
+        out[f] = {"median": float(e.median()), "max": float(e.max())}
+    return out
+
+
+def _statistics(a: dict, b: dict, ny: int) -> dict:
+    out = {}
     for f in ("rho", "p"):
-        st = vlbm.stats_w1_mean_std(mo["mixed"][f], mo["fp64"][f])
-        out["statistics_rel_l1"][f] = {
+        st = vlbm.stats_w1_mean_std(a[f], b[f])
+        out[f] = {
             "mean": float((st["mean_a"] - st["mean_b"]).abs().sum() / st["mean_b"].abs().sum()),
             "std": float((st["std_a"] - st["std_b"]).abs().sum() / st["std_b"].abs().sum()),
             "w1_over_mean": float(st["w1"].sum() / st["mean_b"].abs().sum()),
         }
         if f == "rho":
             axis = st["w1"][ny // 2 - 1: ny // 2 + 1].mean(0)
-            out["w1_axis_rho"] = {"x": [float(i * 2.5 / nx) for i in range(0, nx, max(1, nx // 16))],
-                                  "w1": [float(axis[i]) for i in range(0, nx, max(1, nx // 16))],
-                                  "mean_over_axis": float(axis.mean())}
-    for e in ens.values():
+            out["w1_axis_rho_mean"] = float(axis.mean())
+    return out
+
+
+def precision_study(nx: int = 2560, ny: int = 1280, M: int = 64, t: float = 0.0035, control: bool = False) -> dict:
+    """Mixed against FP64, seed-matched.  With control, a third FP64 ensemble
+    whose amplitudes differ by 1e-7 relative measures how far two precise
+    runs drift apart by the same horizon (the pathwise divergence of the jet):
+    the mixed path is as good as a precise path when its differences are of
+    that size."""
+    runs = {"mixed": ("mixed", vlbm.PerturbParams()), "fp64": ("fp64", vlbm.PerturbParams())}
+    if control:
+        amp = [0.1 * k ** -2.0 * (1.0 + 1e-7) for k in range(1, 11)]
+        runs["fp64_perturbed"] = ("fp64", vlbm.PerturbParams(amp=amp))
+    secs, steps, mo = {}, {}, {}
+    for name, (prec, pert) in runs.items():
+        e = vlbm.Ensemble([(nx, ny)], precision=prec)
+        e.init(0, M, pert)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(e.stream):
+            a.record(e.stream)
+            e.advance_to(t)
+            b.record(e.stream)
+        b.synchronize()
+        secs[name] = a.elapsed_time(b) / 1e3
+        steps[name] = e.time(0)[1]
+        mo[name] = e.moments(0)
         e.close()
+    out = {"study": "precision: mixed vs FP64, seed-matched", "nx": nx, "ny": ny, "M": M, "t": t,
+           "steps": {p: [int(s.min()), int(s.max())] for p, s in steps.items()},
+           "seconds": secs,
+           "cell_updates_per_s": {p: float(nx * ny * steps[p].sum() / secs[p]) for p in secs},
+           "mixed_vs_fp64": {"pathwise_rel_l1": _pathwise(mo["mixed"], mo["fp64"]),
+                             "statistics_rel_l1": _statistics(mo["mixed"], mo["fp64"], ny)}}
+    if control:
+        out["fp64_perturbed_vs_fp64"] = {"amplitude_change": 1e-7,
+                                         "pathwise_rel_l1": _pathwise(mo["fp64_perturbed"], mo["fp64"]),
+                                         "statistics_rel_l1": _statistics(mo["fp64_perturbed"], mo["fp64"], ny)}
     return out
 
 
@@ -132,10 +152,11 @@ def rate(h, err) -> float | None:
     return float(np.polyfit(np.log(h), np.log(err), 1)[0])
 
 
-def _functionals(a: torch.Tensor, b: torch.Tensor, stream) -> dict:
-    f = vlbm.stats_error_functionals(a, b, stream=stream)
+def _functionals(a: torch.Tensor, b: torch.Tensor, npd: int = 10) -> dict:
+    f = vlbm.stats_error_functionals(a, b)
     e_mean, e_std, w11, e_strong = (float(x) for x in f.cpu())
-    return {"W_11": w11, "E_mean": e_mean, "E_std": e_std, "E_strong": e_strong}
+    w12, _ = vlbm.stats_w1_two_point(a, b, npd)
+    return {"W_11": w11, "W_12": float(w12), "E_mean": e_mean, "E_std": e_std, "E_strong": e_strong}
 
 
 def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPER, precision: str = "mixed") -> dict:
@@ -148,7 +169,7 @@ def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPE
     out = {"study": "Cauchy and reference convergence on the paper's ladder", "domain": "[0, 2.5] x [-1, 1]",
            "M": M, "precision": precision, "levels": [list(lv) for lv in levels],
            "common_grid": [nx0, ny0], "snapshots": []}
-    keys = ("W_11", "E_mean", "E_std", "E_strong")
+    keys = ("W_11", "W_12", "E_mean", "E_std", "E_strong")
     for t in times:
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(ens.stream):
@@ -158,18 +179,20 @@ def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPE
         b.synchronize()
         sec = a.elapsed_time(b) / 1e3
         steps = [ens.time(l)[1] for l in range(len(levels))]
+        # the binding orders the caller's current stream after the ensemble's
+        # work; restriction and functionals then run on that stream
         common = []
         for l, (nx, ny) in enumerate(levels):
             d = ens.density(l, f32=False)
-            common.append(vlbm.stats_restrict(d, nx // nx0, stream=ens.stream) if nx != nx0 else d)
+            common.append(vlbm.stats_restrict(d, nx // nx0) if nx != nx0 else d)
             del d
         snap = {"t": t, "seconds": sec, "steps": [[int(s.min()), int(s.max())] for s in steps],
                 "cauchy": [], "reference": []}
         L = len(levels) - 1
         for l in range(1, L + 1):
-            snap["cauchy"].append({"pair": [levels[l - 1][0], levels[l][0]], **_functionals(common[l - 1], common[l], ens.stream)})
+            snap["cauchy"].append({"pair": [levels[l - 1][0], levels[l][0]], **_functionals(common[l - 1], common[l])})
         for l in range(L):
-            snap["reference"].append({"pair": [levels[l][0], levels[L][0]], **_functionals(common[l], common[L], ens.stream)})
+            snap["reference"].append({"pair": [levels[l][0], levels[L][0]], **_functionals(common[l], common[L])})
         dx = [2.5 / nx for nx, _ in levels]
         snap["rates"] = {
             "cauchy": {k: rate(dx[:L], [p[k] for p in snap["cauchy"]]) for k in keys},
@@ -192,11 +215,12 @@ def main(argv=None):
     ap.add_argument("--t", type=float, default=0.0035, help="final time (precision study)")
     ap.add_argument("--times", type=str, default="0.0005,0.001,0.002,0.0035", help="snapshot times (cauchy)")
     ap.add_argument("--peak-gbs", type=float, default=None)
+    ap.add_argument("--control", action="store_true", help="precision: add a perturbed FP64 control run")
     args = ap.parse_args(argv)
     if args.study == "ladder":
         res = ladder(args.precision or "fp64", args.steps, M=args.M or 1, peak_gbs=args.peak_gbs)
     elif args.study == "precision":
-        res = precision_study(args.nx, args.ny, args.M or 64, args.t)
+        res = precision_study(args.nx, args.ny, args.M or 64, args.t, args.control)
     else:
         res = cauchy(args.M or 64, [float(x) for x in args.times.split(",")], precision=args.precision or "mixed")
     print(json.dumps(res), flush=True)

@@ -31,8 +31,9 @@ EXPORTED = [
     "vlbm_init_ensemble_block", "vlbm_init_ensemble_samples", "vlbm_kernel_launches", "vlbm_step",
     "vlbm_advance_to", "vlbm_moments", "vlbm_density", "vlbm_time", "vlbm_sync", "vlbm_get_state",
     "vlbm_set_state", "stats_w1_mean_std", "stats_error_functionals", "stats_error_functionals_noalloc",
-    "stats_quantiles", "stats_histogram", "stats_restrict",
-    "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_step_design", "vlbm_destroy",
+    "stats_quantiles", "stats_histogram", "stats_restrict", "stats_w1_two_point",
+    "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_step_design", "vlbm_grad_amplitudes", "vlbm_amplitudes",
+    "vlbm_check_bounded_wait", "vlbm_destroy",
 ]
 
 
@@ -105,10 +106,14 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "stats_quantiles": ([p, i, i, i, i, p, i, p, p], i),
         "stats_histogram": ([p, i, i, i, i, p, i, p, p], i),
         "stats_restrict": ([p, i, i, i, i, i, p, i, p], i),
+        "stats_w1_two_point": ([p, i, i, i, p, i, i, i, i, i, p, p, p], i),
         "vlbm_save": ([p, p, ctypes.POINTER(ctypes.c_size_t)], i),
         "vlbm_load": ([p, p, ctypes.c_size_t], i),
         "vlbm_last_error": ([p], ctypes.c_char_p),
         "vlbm_step_design": ([p, p, ctypes.POINTER(ctypes.c_char_p), p], i),
+        "vlbm_grad_amplitudes": ([p, i, i, p, p, p], i),
+        "vlbm_amplitudes": ([p, p, p], i),
+        "vlbm_check_bounded_wait": ([d], i),
         "vlbm_destroy": ([p], None),
     }
     for name, (args, res) in sig.items():
@@ -316,6 +321,28 @@ class Ensemble:
     def sync(self):
         self._call(self.lib.vlbm_sync)
 
+    def amplitudes(self) -> np.ndarray:
+        """Per-mode amplitudes of the last initialisation (Eq. (karhunenExp))."""
+        K = ctypes.c_int(0)
+        _check(self.lib.vlbm_amplitudes(self.ctx, None, ctypes.byref(K)), self.ctx)
+        amp = np.zeros(K.value)
+        _check(self.lib.vlbm_amplitudes(self.ctx, amp.ctypes.data_as(ctypes.c_void_p), None), self.ctx)
+        return amp
+
+    def grad_amplitudes(self, nsteps: int, w: torch.Tensor, checkpoint_every: int = 20):
+        """(J, dJ/da) for J = (1/M) sum_m sum w rho_m after nsteps FP64 steps from the
+        initial state of the last initialisation (hand-written discrete adjoint,
+        checkpoint-and-recompute every checkpoint_every steps).  w [ny, nx]."""
+        ny, nx = self.shape(0)
+        w = w.to(self.device, torch.float64).contiguous()
+        if tuple(w.shape) != (ny, nx):
+            raise ValueError(f"w must be [{ny}, {nx}]")
+        grad = np.zeros(len(self.amplitudes()))
+        J = ctypes.c_double(0.0)
+        self._call(self.lib.vlbm_grad_amplitudes, int(nsteps), int(checkpoint_every), _ptr(w), ctypes.byref(J),
+                   grad.ctypes.data_as(ctypes.c_void_p))
+        return J.value, grad
+
     def step_design(self):
         """(index, name, count) of the mixed step kernel's launch design; index
         -1 before the first step or for FP64."""
@@ -348,6 +375,13 @@ class Ensemble:
     def load(self, blob: bytes):
         buf = (ctypes.c_ubyte * len(blob)).from_buffer_copy(blob)
         self._call(self.lib.vlbm_load, buf, len(blob))
+
+
+def check_bounded_wait(limit_s: float = 0.05) -> int:
+    """Status of one device wait that nothing completes, bounded by limit_s
+    (VLBM_ETIMEOUT = 6 is the designed outcome)."""
+    _require_cuda()
+    return int(load_library().vlbm_check_bounded_wait(float(limit_s)))
 
 
 def kernel_launches() -> int:
@@ -387,6 +421,25 @@ def stats_restrict(ens: torch.Tensor, r: int, f32: bool = False, stream: torch.c
     _check(lib.stats_restrict(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, r, _ptr(out), int(f32),
                               ctypes.c_void_p(s.cuda_stream)))
     return out
+
+
+def stats_w1_two_point(ens_a: torch.Tensor, ens_b: torch.Tensor, npd: int = 10,
+                       stream: torch.cuda.Stream | None = None):
+    """Two-point Wasserstein distance W_{1,2} (Sec. 3.4) between [M, ny, nx] and
+    [M, r ny, r nx] on the npd x npd subsample: (mean as a 0-d device tensor,
+    per-pair values [npd^4])."""
+    _require_cuda()
+    lib = load_library()
+    ens_a, ens_b = ens_a.contiguous(), ens_b.contiguous()
+    M, nya, nxa = ens_a.shape
+    _, nyb, nxb = ens_b.shape
+    w = torch.empty((), dtype=torch.float64, device=ens_a.device)
+    pairs = torch.empty(npd ** 4, dtype=torch.float64, device=ens_a.device)
+    s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
+    _check(lib.stats_w1_two_point(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
+                                  int(ens_b.dtype == torch.float32), nxb, nyb, M, npd, _ptr(w), _ptr(pairs),
+                                  ctypes.c_void_p(s.cuda_stream)))
+    return w, pairs
 
 
 def stats_error_functionals(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cuda.Stream | None = None):
@@ -449,3 +502,44 @@ def stats_histogram(ens: torch.Tensor, edges: torch.Tensor, stream: torch.cuda.S
     _check(lib.stats_histogram(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, _ptr(e), e.numel() - 1,
                                _ptr(out), ctypes.c_void_p(s.cuda_stream)))
     return out
+
+
+def axial_weights(ny: int, nx: int, g: torch.Tensor | None = None) -> torch.Tensor:
+    """w [ny, nx] of the axial density: 1/2 on rows ny/2 - 1 and ny/2 (the two
+    rows next to y = 0), times the column weights g [nx] (ones by default)."""
+    w = torch.zeros((ny, nx), dtype=torch.float64)
+    g = torch.ones(nx, dtype=torch.float64) if g is None else g.detach().to("cpu", torch.float64)
+    w[ny // 2 - 1] = 0.5 * g
+    w[ny // 2] = 0.5 * g
+    return w
+
+
+class AxialMeanDensity(torch.autograd.Function):
+    """Axial ensemble-mean density after nsteps FP64 steps as a differentiable
+    function of the K per-mode KL amplitudes (Sec. 2.3, Eq. (karhunenExp)).
+
+    forward(amp [K], grid (nx, ny), M, nsteps, seed, checkpoint_every) -> [nx]
+    backward runs the library's adjoint (vlbm_grad_amplitudes) with the
+    incoming gradient as column weights.  Valid over windows shorter than the
+    pathwise-divergence time of the realizations."""
+
+    @staticmethod
+    def forward(ctx, amp, grid, M, nsteps, seed=0, checkpoint_every=20):
+        nx, ny = grid
+        a = amp.detach().to("cpu", torch.float64)
+        ens = Ensemble([(nx, ny)], precision="fp64")
+        ens.init(seed, M, PerturbParams(K=len(a), amp=[float(x) for x in a]))
+        ens.step(nsteps)
+        rho = ens.density(0, f32=False)
+        axial = 0.5 * (rho[:, ny // 2 - 1] + rho[:, ny // 2]).mean(0)
+        ctx.ens, ctx.nsteps, ctx.every = ens, nsteps, checkpoint_every
+        return axial.to(amp.device, amp.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        ens = ctx.ens
+        ny, nx = ens.shape(0)
+        _, grad = ens.grad_amplitudes(ctx.nsteps, axial_weights(ny, nx, g), ctx.every)
+        ens.close()
+        ctx.ens = None
+        return torch.from_numpy(grad).to(g.device, g.dtype), None, None, None, None, None

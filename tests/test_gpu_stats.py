@@ -100,3 +100,28 @@ def test_sharded_statistics_single_process_equal_direct():
             assert torch.equal(got[k], want[k]), k
     finally:
         dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("M, r, npd, f32", [(7, 1, 3, False), (64, 2, 4, True), (33, 3, 2, False), (1, 1, 2, False)])
+def test_two_point_w1_matches_oracle(M, r, npd, f32):
+    # Eq. (w2): exact optimal assignment per point pair against scipy's
+    rng = np.random.default_rng(M + r)
+    ny, nx = 9, 11
+    a = rng.lognormal(0.0, 0.5, (M, ny, nx))
+    b = rng.lognormal(0.1, 0.4, (M, ny * r, nx * r))
+    if f32:
+        a, b = a.astype(np.float32), b.astype(np.float32)
+    w, pairs = vlbm.stats_w1_two_point(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), npd)
+    want, want_pairs = O.w1_two_point(a.astype(np.float64), b.astype(np.float64), npd)
+    assert np.allclose(pairs.cpu().numpy(), want_pairs, rtol=1e-12, atol=1e-15)
+    assert abs(float(w) - want) <= 1e-12 * want
+
+
+def test_two_point_w1_identities():
+    rng = np.random.default_rng(2)
+    a = torch.from_numpy(rng.lognormal(size=(20, 8, 8))).cuda()
+    w, pairs = vlbm.stats_w1_two_point(a, a, 4)
+    assert float(w) == 0.0
+    # a translated copy: every joint law moves by (0.1, 0.1)
+    w, pairs = vlbm.stats_w1_two_point(a, a + 0.1, 4)
+    assert torch.allclose(pairs, torch.full_like(pairs, 0.1 * np.sqrt(2.0)), rtol=1e-12)

@@ -11,6 +11,7 @@ moments; the restriction against conservation of the integral.
 import itertools
 
 import numpy as np
+import pytest
 
 from oracle import oracle as O
 from tests import inputs
@@ -106,3 +107,59 @@ def test_statistics_between_levels_restrict_first():
     assert np.allclose(mb, b.mean(axis=0), rtol=1e-14)
     assert np.allclose(sb, b.std(axis=0), rtol=1e-13)
     assert np.allclose(w1, np.abs(np.sort(a, 0) - np.sort(b, 0)).mean(0), rtol=1e-14)
+
+
+# --- two-point Wasserstein distance (Sec. 3.4, Eq. (w2)) ----------------------
+
+
+def _brute_w1_2d(a, b):
+    import itertools
+
+    M = len(a)
+    best = np.inf
+    for perm in itertools.permutations(range(M)):
+        best = min(best, sum(np.hypot(*(a[i] - b[perm[i]])) for i in range(M)))
+    return best / M
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 5, 6])
+def test_w1_2d_equals_brute_force(M):
+    rng = np.random.default_rng(M)
+    a, b = rng.normal(size=(M, 2)), rng.normal(size=(M, 2))
+    assert abs(O.w1_points_2d(a, b) - _brute_w1_2d(a, b)) <= 1e-14 * max(1.0, _brute_w1_2d(a, b))
+
+
+def test_w1_2d_on_the_diagonal_is_sqrt2_times_sorted_1d():
+    # points (s, s) and (t, t): distance sqrt(2)|s - t|, the sorted matching is optimal
+    rng = np.random.default_rng(7)
+    s, t = rng.lognormal(size=40), rng.lognormal(size=40)
+    want = np.sqrt(2.0) * np.abs(np.sort(s) - np.sort(t)).mean()
+    got = O.w1_points_2d(np.stack([s, s], 1), np.stack([t, t], 1))
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_w1_2d_of_a_translation_is_its_length():
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=(30, 2))
+    c = np.array([0.3, -0.4])
+    assert abs(O.w1_points_2d(a, a + c) - 0.5) <= 1e-12
+
+
+def test_two_point_distance_structure():
+    rng = np.random.default_rng(11)
+    M, ny, nx, npd = 6, 8, 10, 3
+    a = rng.lognormal(size=(M, ny, nx))
+    w, pairs = O.w1_two_point(a, a, npd)
+    assert w == 0.0 and pairs.shape == (npd ** 4,)
+    pts = O.two_point_points(nx, ny, npd)
+    assert pts[0] == (1, 1) and pts[-1] == (8, 6) and len(set(pts)) == npd * npd
+    # a fine ensemble that restricts to a + 0.1 everywhere: every joint law is translated by (0.1, 0.1)
+    fine = np.repeat(np.repeat(a + 0.1, 2, axis=1), 2, axis=2)
+    w, pairs = O.w1_two_point(a, fine, npd)
+    assert np.allclose(pairs, 0.1 * np.sqrt(2.0), rtol=1e-12)
+    # diagonal pairs (k, k) reduce to sqrt(2) times the one-point W1 at that cell
+    b = rng.lognormal(size=(M, ny, nx))
+    w, pairs = O.w1_two_point(a, b, npd)
+    for k, (i, j) in enumerate(pts):
+        one = np.abs(np.sort(a[:, j, i]) - np.sort(b[:, j, i])).mean()
+        assert abs(pairs[k * len(pts) + k] - np.sqrt(2.0) * one) <= 1e-12 * max(one, 1e-300)
