@@ -93,11 +93,26 @@ struct Ctx {
 };
 
 __device__ __forceinline__ float4 f4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
-__device__ __forceinline__ float4 add(float4 a, float4 b) { return f4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ __forceinline__ float4 sub(float4 a, float4 b) { return f4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-__device__ __forceinline__ float4 scale(float s, float4 x) { return f4(s * x.x, s * x.y, s * x.z, s * x.w); }
+// Component-wise float4 arithmetic on packed FP32 pairs (sm_100 and later):
+// each packed operation is, per component, the same IEEE operation as its
+// scalar form (a - b = a + (-b) exactly), so results are unchanged and each
+// float4 operation issues two instructions instead of four.
+__device__ __forceinline__ float2 lo2(const float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(const float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 cat4(const float2 l, const float2 h) { return f4(l.x, l.y, h.x, h.y); }
+__device__ __forceinline__ float4 add(float4 a, float4 b) {
+  return cat4(__fadd2_rn(lo2(a), lo2(b)), __fadd2_rn(hi2(a), hi2(b)));
+}
+__device__ __forceinline__ float4 sub(float4 a, float4 b) {
+  return cat4(__fadd2_rn(lo2(a), make_float2(-b.x, -b.y)), __fadd2_rn(hi2(a), make_float2(-b.z, -b.w)));
+}
+__device__ __forceinline__ float4 scale(float s, float4 x) {
+  const float2 ss = make_float2(s, s);
+  return cat4(__fmul2_rn(ss, lo2(x)), __fmul2_rn(ss, hi2(x)));
+}
 __device__ __forceinline__ float4 axpy(float s, float4 x, float4 y) {
-  return f4(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z), fmaf(s, x.w, y.w));
+  const float2 ss = make_float2(s, s);
+  return cat4(__ffma2_rn(ss, lo2(x), lo2(y)), __ffma2_rn(ss, hi2(x), hi2(y)));
 }
 
 // B_w u of a node with primitive state P; d = velocity relative to w.
