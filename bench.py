@@ -156,11 +156,12 @@ class OraclePool:
         self.ex.shutdown()
 
 
-def workload_config(levels, M, S, prec):
+def workload_config(levels, M, horizon, prec):
     nxa = " + ".join(f"{nx}x{ny}" for nx, ny in levels)
     return {"workload": f"Mach 2000 jet ensemble, M={M} per GPU, levels {nxa} in one launch, {prec}, R-theta "
-                        f"limiter, {S} VLBM steps + init + density + W1/mean/std statistics per bench step",
-            "levels": levels, "M_per_gpu": M, "solver_steps_per_step": S, "precision": prec,
+                        f"limiter, per bench step: init + every realization {horizon} + density + "
+                        f"W1/mean/std statistics between the levels",
+            "levels": levels, "M_per_gpu": M, "horizon": horizon, "precision": prec,
             "l2": "inputs larger than L2 (lattice state "
                   f"{sum(nx * ny for nx, ny in levels) * M * BYTES_PER_UPDATE[prec] / 1e9:.0f} GB)"}
 
@@ -191,7 +192,8 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox jet ensemble)",
         "impl": "reference",
-        "config": workload_config(levels, args.m, args.solver_steps, args.precision),
+        "config": workload_config(levels, args.m, f"to t = {args.t_final} (landing rule)" if args.t_final > 0
+                                  else f"{args.solver_steps} VLBM steps", args.precision),
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": pool.workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -222,7 +224,7 @@ def run_ours(args):
     prec = args.precision
     ens = vlbm.Ensemble(levels, precision=prec, stream=stream)
     m_begin = rank * M
-    cells_per_solver_step = sum(nx * ny for nx, ny in levels) * M
+    horizon = f"to t = {args.t_final} (landing rule)" if args.t_final > 0 else f"{S} VLBM steps"
     (nxa, nya), (nxb, nyb) = levels
     dens_a = torch.empty((M, nya, nxa), dtype=torch.float32, device=dev)
     dens_b = torch.empty((M, nyb, nxb), dtype=torch.float32, device=dev)
@@ -231,19 +233,31 @@ def run_ours(args):
     # Eq. (karhunenExp)), uniform on (-1, 1), in pinned host memory
     K = vlbm.PerturbParams().K
     rng = np.random.default_rng(SEED + rank)
-    host_xi = [torch.from_numpy(rng.uniform(-1.0, 1.0, (M, 2 * K))).pin_memory() for _ in range(2)]
+    host_xi = torch.from_numpy(rng.uniform(-1.0, 1.0, (M, 2 * K))).pin_memory()
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     step_ms = []
 
-    def bench_step(e2e: bool, timed: bool, it: int = 0):
+    def advance():
+        # the hot path of one bench step: every realization of both levels to
+        # the paper's final time (landing rule), or a fixed number of steps
+        if args.t_final > 0:
+            ens.advance_to(args.t_final)
+        else:
+            ens.step(S)
+
+    def cells_done() -> int:
+        # cell-updates of the run just finished (realizations take different step counts)
+        return sum(nx * ny * int(ens.time(l)[1].sum()) for l, (nx, ny) in enumerate(levels))
+
+    def bench_step(e2e: bool, timed: bool):
         if e2e:
-            ens.init_samples(host_xi[it % 2])
+            ens.init_samples(host_xi)
         else:
             ens.init(SEED, M, m_begin=m_begin)
         if timed:
             ev[0].record(stream)
-        ens.step(S)
+        advance()
         if timed:
             ev[1].record(stream)
         ens.density(0, out=dens_a)
@@ -264,17 +278,19 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def timed_loop(e2e: bool):
-        for w in range(args.warmup):
-            bench_step(e2e, False, w)
+    def timed_loop(e2e: bool, warmup: int):
+        for _ in range(warmup):
+            bench_step(e2e, False)
+        # every bench step repeats the same inputs: its cell-updates are those of the warm-up
+        cells = cells_done()
         barrier()
         launches0 = vlbm.kernel_launches()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         h0 = time.perf_counter()
         t0.record(stream)
-        for it in range(args.steps):
-            bench_step(e2e, not e2e, it)
+        for _ in range(args.steps):
+            bench_step(e2e, not e2e)
             if not e2e:
                 torch.cuda.synchronize()
                 step_ms.append(ev[0].elapsed_time(ev[1]))
@@ -284,16 +300,23 @@ def run_ours(args):
         ms = t0.elapsed_time(t1) if not e2e else (time.perf_counter() - h0) * 1e3
         launches = vlbm.kernel_launches() - launches0
         if dist is not None:
-            tt = torch.tensor([ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
-        return ms, launches
+            tt = torch.tensor([ms, float(cells)], dtype=torch.float64, device=dev)
+            mx = tt.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+            ms, cells_all = float(mx[0].item()), int(tt[1].item())
+        else:
+            cells_all = cells
+        return ms, launches, cells, cells_all
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms, launches = timed_loop(False)
+    ms, launches, cells_step, cells_all = timed_loop(False, args.warmup)
     clk = clocks.stop()
-    ms_e2e, _ = timed_loop(True)
+    # the system is warm: one untimed end-to-end step, then the timed ones
+    ms_e2e, _, _, cells_all_e2e = timed_loop(True, 1)
+    run_steps = {f"{nx}x{ny}": [int(ens.time(l)[1].min()), int(ens.time(l)[1].max())]
+                 for l, (nx, ny) in enumerate(levels)}
     design = ens.step_design()
 
     # the FP64 path on the same levels, fewer realizations (rate per cell update)
@@ -336,12 +359,13 @@ def run_ours(args):
         ens_m.close()
         ens_d.close()
 
-    total_cells = cells_per_solver_step * S * args.steps * world
-    value = total_cells / (ms / 1e3) / 1e9
-    e2e_value = total_cells / (ms_e2e / 1e3) / 1e9
+    value = cells_all * args.steps / (ms / 1e3) / 1e9
+    e2e_value = cells_all_e2e * args.steps / (ms_e2e / 1e3) / 1e9
     hbm, src = peaks()
-    kern_s = float(np.mean(step_ms)) / 1e3 / S
-    achieved = BYTES_PER_UPDATE[prec] * cells_per_solver_step / kern_s / 1e9
+    # the step kernels of one bench step: algorithmic bytes of its cell-updates
+    # over the CUDA-event time of the whole advance (ticks, landing included)
+    adv_s = float(np.mean(step_ms)) / 1e3
+    achieved = BYTES_PER_UPDATE[prec] * cells_step / adv_s / 1e9
     sha = kernel_sha(prec)
     tr = NCU_TRAFFIC.get(prec)
     traffic = tr["bytes_per_launch"] if tr and tr["sha"] == sha and tr["design"] == design[1] else None
@@ -361,13 +385,17 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
             "data": "synthetic (seeded Philox4x32-10 Karhunen-Loeve jet inlets)",
-            "config": workload_config(levels, M, S, prec),
+            "config": {**workload_config(levels, M, horizon, prec), "steps_per_realization": run_steps,
+                       "cell_updates_per_step": cells_step},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": f"step_{prec}_kernel", "design": design[1], "peak_source": f"{src} hbm_gbs",
                          "bytes_per_cell_update": BYTES_PER_UPDATE[prec],
-                         "note": "kernel time = CUDA-event time of the S-step graph / S (includes the "
-                                 "per-step tick kernel)"},
+                         "advance_ms": adv_s * 1e3,
+                         "note": "achieved = 160 B x cell-updates of one bench step / CUDA-event time of its "
+                                 "advance (every step launch, tick and landing check; realizations that "
+                                 "landed leave the launches); traffic: ncu DRAM bytes of one launch with "
+                                 "every realization active"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": M * 2 * K * 8,
                     "d2h_bytes_per_step": 5 * nxa * nya * 8,
@@ -389,12 +417,14 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--m", type=int, default=M_PER_GPU)
-    ap.add_argument("--solver-steps", type=int, default=64)
+    ap.add_argument("--solver-steps", type=int, default=64,
+                    help="fixed steps per bench step when --t-final is 0; the statistic-error check's horizon")
+    ap.add_argument("--t-final", type=float, default=0.0035, help="advance every realization to this time")
     ap.add_argument("--fp64-m", type=int, default=50)
     ap.add_argument("--fp64-steps", type=int, default=8)
     ap.add_argument("--stat-m", type=int, default=16)

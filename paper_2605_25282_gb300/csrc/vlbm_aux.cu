@@ -128,11 +128,20 @@ __device__ __forceinline__ bool node_of(const LevelDesc& D, int& i, int& j) {
   return true;
 }
 
-__global__ void init_state_kernel(const Launch L, int precision) {
+// amb: the ambient state at rest as FP32 primitives, formed once on the host
+// (the FP32 path writes it without FP64 arithmetic per node).
+__global__ void init_state_kernel(const Launch L, int precision, float4 amb) {
   const LevelDesc& D = L.lv[blockIdx.z];
   const int m = blockIdx.y;
   int i, j;
   if (!node_of(D, i, j)) return;
+  if (precision != VLBM_FP64 && i != 0) {
+    float4* s = reinterpret_cast<float4*>(D.lat) + (size_t)m * D.real_stride;
+    const size_t off = (size_t)j * D.nx_pad + i;
+    s[off] = amb;
+    for (int k = 0; k < 4; ++k) s[(1 + k) * D.plane + off] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
   const double gamma = L.ph.gamma;
   double q[4];
   if (i == 0) {
@@ -150,13 +159,8 @@ __global__ void init_state_kernel(const Launch L, int precision) {
     for (int c = 0; c < 4; ++c) s[c * D.plane + off] = q[c];
   } else {
     float4* s = reinterpret_cast<float4*>(D.lat) + (size_t)m * D.real_stride;
-    double v1 = 0.0, v2 = 0.0, p;
-    if (i == 0) {
-      cons_to_prim(q, gamma, v1, v2, p);
-    } else {
-      // the ambient state at rest: cons_to_prim reduces exactly to this
-      p = (gamma - 1.0) * q[3];
-    }
+    double v1, v2, p;
+    cons_to_prim(q, gamma, v1, v2, p);
     s[off] = make_float4((float)q[0], (float)v1, (float)v2, (float)p);
     for (int k = 0; k < 4; ++k) s[(1 + k) * D.plane + off] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -194,29 +198,22 @@ __global__ void lambda_kernel(const Launch L, int precision, int level, int m0) 
   if (node_of(D, i, j)) {
     const int par = (int)(rs->steps & 1);
     const size_t off = (size_t)j * D.nx_pad + i;
-    double rho, v1, v2, p;
     if (precision == VLBM_FP64) {
       const double* s = reinterpret_cast<const double*>(D.lat) + ((size_t)par * L.M + m) * D.real_stride;
-      double q[4];
+      double q[4], v1, v2, p;
       for (int c = 0; c < 4; ++c) q[c] = s[c * D.plane + off];
-      rho = q[0];
+      const double rho = q[0];
       cons_to_prim(q, L.ph.gamma, v1, v2, p);
+      if (!(rho > 0.0) || !(p > 0.0)) flags |= 1;
+      if (!isfinite(rho) || !isfinite(v1) || !isfinite(v2) || !isfinite(p)) flags |= 2;
+      if (!flags) lam = fmax(fabs(v1), fabs(v2)) + sqrt(L.ph.gamma * p / rho);
     } else {
+      // FP32 throughout (the stored state is FP32); the value is exact in FP64
       const float4* s = reinterpret_cast<const float4*>(D.lat) + ((size_t)par * L.M + m) * D.real_stride;
       const float4 w = s[off];
-      rho = w.x;
-      v1 = w.y;
-      v2 = w.z;
-      p = w.w;
-    }
-    if (!(rho > 0.0) || !(p > 0.0)) flags |= 1;
-    if (!isfinite(rho) || !isfinite(v1) || !isfinite(v2) || !isfinite(p)) flags |= 2;
-    if (!flags) {
-      if (precision == VLBM_FP64)
-        lam = fmax(fabs(v1), fabs(v2)) + sqrt(L.ph.gamma * p / rho);
-      else
-        lam = (double)(fmaxf(fabsf((float)v1), fabsf((float)v2)) +
-                       sqrtf((float)L.ph.gamma * (float)p / (float)rho));
+      if (!(w.x > 0.0f) || !(w.w > 0.0f)) flags |= 1;
+      if (!isfinite(w.x) || !isfinite(w.y) || !isfinite(w.z) || !isfinite(w.w)) flags |= 2;
+      if (!flags) lam = (double)(fmaxf(fabsf(w.y), fabsf(w.z)) + sqrtf(L.pf.gamma * w.w / w.x));
     }
   }
   unsigned long long b = lam_to_bits(lam);
@@ -594,7 +591,11 @@ cudaError_t launch_init_state(const Launch& L, int precision, cudaStream_t s) {
     Launch one = L;
     one.lv[0] = L.lv[l];
     dim3 g = node_grid(L.lv[l], L.M);
-    init_state_kernel<<<g, kThreads, 0, s>>>(one, precision);
+    // cons_to_prim of the ambient state at rest reduces exactly to
+    // (rho, 0, 0, (gamma - 1) E) with E = p / (gamma - 1) + 0
+    const double E = L.ph.amb_p / (L.ph.gamma - 1.0) + 0.0;
+    const float4 amb = make_float4((float)L.ph.amb_rho, 0.0f, 0.0f, (float)((L.ph.gamma - 1.0) * E));
+    init_state_kernel<<<g, kThreads, 0, s>>>(one, precision, amb);
   }
   return cudaGetLastError();
 }

@@ -152,9 +152,9 @@ __device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float
 // cancellation in the pressure quadratic).  The floors eps_rho, eps_p are
 // min(value, max(eps_pos, 1e-5 value)) of the first-order state U0: the
 // relative margin keeps the final average admissible despite FP32 rounding.
-// theta = 1 is tested first, inline and without any division (the common
-// case); the general case is a call.  The constants come by value so that no
-// context struct lives in local memory.
+// theta = 1 is tested first, inline and without any division (theta_one, the
+// common case); the general case is a call.  The constants come by value so
+// that no context struct lives in local memory.
 __device__ __noinline__ float theta_star_general(const float4 U0, const float4 D, float lower, float hi_b,
                                                  float kk) {
   float th = 1.0f;
@@ -187,11 +187,11 @@ __device__ __noinline__ float theta_star_general(const float4 U0, const float4 D
 }
 
 // b holds the node's limits, computed once per node by node_p2.
-__device__ __forceinline__ float theta_star(const float4 U0, const float4 D, const Bnd b) {
+// theta = 1 admissible: V = U0 + D inside the density limits with
+// q(1) = rho E - |m|^2 / 2 - kk rho >= 0.
+__device__ __forceinline__ bool theta_one(const float4 U0, const float4 D, const Bnd b) {
   const float4 V = add(U0, D);
-  // q(theta) = rho E - |m|^2 / 2 - kk rho at theta = 1
-  if (V.x >= b.lo && V.x <= b.hi && fmaf(V.x, V.w - b.kk, -0.5f * fmaf(V.y, V.y, V.z * V.z)) >= 0.0f) return 1.0f;
-  return theta_star_general(U0, D, b.lo, b.hi, b.kk);
+  return V.x >= b.lo && V.x <= b.hi && fmaf(V.x, V.w - b.kk, -0.5f * fmaf(V.y, V.y, V.z * V.z)) >= 0.0f;
 }
 
 __device__ __forceinline__ bool is_boundary(int i, int j, int nx, int ny) {
@@ -310,8 +310,24 @@ __device__ __forceinline__ float face_theta(const float4 PL, const float4 PR, co
     if (limiter == 1) {
       th = 1.0f;
     } else {
-      const float tL = bL ? 1.0f : theta_star(UL, scale(-4.f, dL), BL);
-      const float tR = bR ? 1.0f : theta_star(UR, scale(4.f, dR), BR);
+      const float4 DL = scale(-4.f, dL), DR = scale(4.f, dR);
+      float tL = 1.0f, tR = 1.0f;
+      // sides whose theta = 1 test fails take the general case; one side per
+      // pass, so a warp runs it as often as its lanes need it most, not once
+      // per side that any lane needs
+      int pend = ((!bL && !theta_one(UL, DL, BL)) ? 1 : 0) | ((!bR && !theta_one(UR, DR, BR)) ? 2 : 0);
+      while (pend) {
+        const bool sl = (pend & 1) != 0;
+        const Bnd b = sl ? BL : BR;
+        const float t = theta_star_general(sl ? UL : UR, sl ? DL : DR, b.lo, b.hi, b.kk);
+        if (sl) {
+          tL = t;
+          pend &= 2;
+        } else {
+          tR = t;
+          pend = 0;
+        }
+      }
       th = fminf(tL, tR);
     }
   }

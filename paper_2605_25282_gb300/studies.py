@@ -4,6 +4,8 @@ paper's Sec. 3-4 that are more than one bench step.
     python -m paper_2605_25282_gb300.studies ladder     [--precision fp64|mixed] [--steps 200]
     python -m paper_2605_25282_gb300.studies precision  [--nx 2560 --ny 1280 --M 64 --t 0.0035]
     python -m paper_2605_25282_gb300.studies cauchy     [--M 64 --times 0.0005,0.001,0.002,0.0035]
+    python -m paper_2605_25282_gb300.studies final      [--M 1000 --t 0.0035] [--save state.bin]
+    python -m paper_2605_25282_gb300.studies resume     --load state.bin [--M 1000 --steps 200]
 
 ladder     one realization per level of the single-realization refinement
            ladder (400x200 ... 5060x2530), fixed steps: cell-updates/s and
@@ -20,6 +22,11 @@ cauchy     the paper's own ladder on [0, 2.5] x [-1, 1] (500x400 ... 4000x3200,
            functionals of Sec. 3.4 (W_11, W_12, E_mean, E_std, E_strong) of the
            Cauchy and the reference comparisons, and their rates (Eq. (ratefit),
            least-squares slope in log-log).
+final      the batched ensemble (M = 1000 of 400x200 + 800x400, mixed, one
+           launch per step) to the paper's final time with the landing rule,
+           then the statistics between the two levels; --save keeps the state.
+resume     a saved state advanced a fixed number of steps (the step kernel on
+           the developed, turbulent flow).
 
 Every run prints one JSON object.  All inputs are synthetic and seeded
 (Philox4x32-10 KL inlets, seed 0, realizations 0..M-1).
@@ -159,6 +166,24 @@ def _functionals(a: torch.Tensor, b: torch.Tensor, npd: int = 10) -> dict:
     return {"W_11": w11, "W_12": float(w12), "E_mean": e_mean, "E_std": e_std, "E_strong": e_strong}
 
 
+def axial_profile(dens: torch.Tensor, x_max: float = 2.5, rho_amb: float = 0.5) -> dict:
+    """Ensemble statistics of the density on the jet axis (rows ny/2 - 1 and
+    ny/2) of one level [M, ny, nx]: the bow-shock position (the largest x
+    where the axial mean exceeds the ambient density by 10 %), the median
+    axial std upstream of x = 1.4, and the peak axial std with the mean
+    there (the quantities Sec. 4 reads off the axis)."""
+    M, ny, nx = dens.shape
+    st = vlbm.stats_w1_mean_std(dens, dens)
+    mean = (0.5 * (st["mean_a"][ny // 2 - 1] + st["mean_a"][ny // 2])).cpu().numpy()
+    std = (0.5 * (st["std_a"][ny // 2 - 1] + st["std_a"][ny // 2])).cpu().numpy()
+    x = np.arange(nx) * (x_max / nx)
+    above = np.nonzero(mean > 1.1 * rho_amb)[0]
+    k = int(np.argmax(std))
+    return {"bow_shock_x": float(x[above[-1]]) if len(above) else 0.0,
+            "axial_std_upstream_median": float(np.median(std[(x > 0.05) & (x < 1.4)])),
+            "axial_std_peak": float(std[k]), "axial_std_peak_x": float(x[k]), "axial_mean_at_peak": float(mean[k])}
+
+
 def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPER, precision: str = "mixed") -> dict:
     """The paper's protocol (Sec. 3.3-3.4): every level's density restricted
     onto the coarsest grid, the Cauchy comparison of successive levels and the
@@ -181,13 +206,14 @@ def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPE
         steps = [ens.time(l)[1] for l in range(len(levels))]
         # the binding orders the caller's current stream after the ensemble's
         # work; restriction and functionals then run on that stream
-        common = []
+        common, axis = [], []
         for l, (nx, ny) in enumerate(levels):
             d = ens.density(l, f32=False)
+            axis.append(axial_profile(d))
             common.append(vlbm.stats_restrict(d, nx // nx0) if nx != nx0 else d)
             del d
         snap = {"t": t, "seconds": sec, "steps": [[int(s.min()), int(s.max())] for s in steps],
-                "cauchy": [], "reference": []}
+                "axis": axis, "cauchy": [], "reference": []}
         L = len(levels) - 1
         for l in range(1, L + 1):
             snap["cauchy"].append({"pair": [levels[l - 1][0], levels[l][0]], **_functionals(common[l - 1], common[l])})
@@ -204,9 +230,69 @@ def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPE
     return out
 
 
+def batched_final_time(M: int = 1000, t: float = 0.0035, levels=((400, 200), (800, 400)),
+                       save: str | None = None) -> dict:
+    """The batched ensemble run to the paper's final time: M realizations of
+    both levels in one launch per step (mixed, landing on t), then the
+    per-cell mean, std and one-point W1 between the levels (the fine level
+    restricted onto the coarse grid) and the error functionals."""
+    levels = [tuple(lv) for lv in levels]
+    ens = vlbm.Ensemble(levels, precision="mixed")
+    ens.init(0, M)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(ens.stream):
+        a.record(ens.stream)
+        ens.advance_to(t)
+        b.record(ens.stream)
+    b.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    steps = [ens.time(l)[1] for l in range(len(levels))]
+    times = [ens.time(l)[0] for l in range(len(levels))]
+    cells = sum(nx * ny * int(s.sum()) for (nx, ny), s in zip(levels, steps))
+    d0, d1 = ens.density(0), ens.density(1)
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record()
+    st = vlbm.stats_w1_mean_std(d0, d1)
+    b2.record()
+    b2.synchronize()
+    f = _functionals(d0, d1)
+    out = {"study": "batched ensemble to the final time", "M": M, "t": t, "levels": [list(lv) for lv in levels],
+           "precision": "mixed", "design": ens.step_design()[1], "seconds": sec, "cell_updates": cells,
+           "GLUPS": cells / sec / 1e9, "steps": [[int(s.min()), int(s.max())] for s in steps],
+           "t_reached": [[float(x.min()), float(x.max())] for x in times],
+           "stats_ms": a2.elapsed_time(b2),
+           "mean_rho_range": [float(st["mean_a"].min()), float(st["mean_a"].max())],
+           "max_std_rho": float(st["std_a"].max()), "w1_cell_mean": float(st["w1"].mean()),
+           "functionals_coarse_vs_fine": f}
+    if save:
+        with open(save, "wb") as fh:
+            fh.write(ens.save())
+        out["saved"] = save
+    ens.close()
+    return out
+
+
+def resume_steps(load: str, M: int, steps: int, levels=((400, 200), (800, 400))) -> dict:
+    """Restores a state written by `final --save` (same levels and M, mixed)
+    and advances it `steps` fixed steps: the step kernel on a developed flow."""
+    levels = [tuple(lv) for lv in levels]
+    ens = vlbm.Ensemble(levels, precision="mixed")
+    ens.init(0, M)
+    with open(load, "rb") as fh:
+        ens.load(fh.read())
+    t0 = [ens.time(l) for l in range(len(levels))]
+    sec = _timed_steps(ens, steps)
+    cells = sum(nx * ny for nx, ny in levels) * M * steps
+    out = {"study": "steps on a restored state", "M": M, "levels": [list(lv) for lv in levels], "steps": steps,
+           "t_start": [float(t[0].min()) for t in t0], "seconds": sec, "GLUPS": cells / sec / 1e9,
+           "GBs": cells * BYTES_PER_UPDATE["mixed"] / sec / 1e9, "design": ens.step_design()[1]}
+    ens.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("study", choices=["ladder", "precision", "cauchy"])
+    ap.add_argument("study", choices=["ladder", "precision", "cauchy", "final", "resume"])
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--M", type=int, default=None)
@@ -216,13 +302,19 @@ def main(argv=None):
     ap.add_argument("--times", type=str, default="0.0005,0.001,0.002,0.0035", help="snapshot times (cauchy)")
     ap.add_argument("--peak-gbs", type=float, default=None)
     ap.add_argument("--control", action="store_true", help="precision: add a perturbed FP64 control run")
+    ap.add_argument("--save", type=str, default=None, help="final: write the final state to this file")
+    ap.add_argument("--load", type=str, default=None, help="resume: the state file written by final --save")
     args = ap.parse_args(argv)
     if args.study == "ladder":
         res = ladder(args.precision or "fp64", args.steps, M=args.M or 1, peak_gbs=args.peak_gbs)
     elif args.study == "precision":
         res = precision_study(args.nx, args.ny, args.M or 64, args.t, args.control)
-    else:
+    elif args.study == "cauchy":
         res = cauchy(args.M or 64, [float(x) for x in args.times.split(",")], precision=args.precision or "mixed")
+    elif args.study == "final":
+        res = batched_final_time(args.M or 1000, args.t, save=args.save)
+    else:
+        res = resume_steps(args.load, args.M or 1000, args.steps)
     print(json.dumps(res), flush=True)
 
 

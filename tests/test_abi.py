@@ -110,3 +110,33 @@ def test_init_samples_rejects_out_of_range_host_values_before_device_work():
         assert idx.value == -1 and name.value == b"none" and cnt.value >= 5
     finally:
         lib.vlbm_destroy(ctx)
+
+
+def test_allocation_failure_is_reported_without_device_work():
+    # host-side fault injection: an allocator that refuses every request
+    lib = vlbm.load_library()
+    arr = (vlbm.Grid * 1)(vlbm.jet_grid(16, 8))
+    jet, amb = vlbm.Prim(5.0, 800.0, 0.0, 0.4127), vlbm.Prim(0.5, 0.0, 0.0, 0.4127)
+    calls = []
+
+    def refuse(nbytes, user):
+        calls.append(nbytes)
+        return None
+
+    def release(ptr, user):
+        pass
+
+    alloc_cb, free_cb = vlbm.ALLOC_FN(refuse), vlbm.FREE_FN(release)
+    ctx = ctypes.c_void_p()
+    # stream handle 1 is the legacy default stream: valid everywhere, no work enqueued here
+    code = lib.vlbm_create(arr, 1, 5 / 3, ctypes.byref(jet), ctypes.byref(amb), None, 1, ctypes.c_void_p(1),
+                           alloc_cb, free_cb, None, ctypes.byref(ctx))
+    assert code == 0, lib.vlbm_last_error(None)
+    try:
+        code = lib.vlbm_init_ensemble(ctx, 0, 4, None)
+        assert code == 2, (code, lib.vlbm_last_error(ctx))  # VLBM_ENOMEM
+        assert "allocation" in lib.vlbm_last_error(ctx).decode() and calls
+        # the context is still usable for calls that need no state
+        assert lib.vlbm_step(ctx, 1) == 7  # VLBM_ESTATE: nothing initialised
+    finally:
+        lib.vlbm_destroy(ctx)
