@@ -157,36 +157,31 @@ __device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float
 // that no context struct lives in local memory.
 __device__ __noinline__ float theta_star_general(const float4 U0, const float4 D, float lower, float hi_b,
                                                  float kk) {
-  float th = 1.0f;
+  // every branch of the rule is evaluated and the taken one selected, so
+  // the lanes of a warp that enter here stay converged
   const float vx = U0.x + D.x;
-  if (vx < lower) {
-    th = __fdividef(U0.x - lower, -D.x);
-  } else if (vx > hi_b) {
-    th = __fdividef(hi_b - U0.x, D.x);
-  }
+  const bool below = vx < lower, above = !below && vx > hi_b;
+  const float lim = __fdividef(below ? U0.x - lower : hi_b - U0.x, below ? -D.x : D.x);
+  float th = (below || above) ? lim : 1.0f;
   th = fminf(fmaxf(th, 0.0f), 1.0f);
   const float C = fmaf(U0.x, U0.w - kk, -0.5f * fmaf(U0.y, U0.y, U0.z * U0.z));
   const float Bq = fmaf(U0.x, D.w, fmaf(D.x, U0.w - kk, -fmaf(U0.y, D.y, U0.z * D.z)));
   const float A = fmaf(D.x, D.w, -0.5f * fmaf(D.y, D.y, D.z * D.z));
-  if (fmaf(th, fmaf(th, A, Bq), C) >= 0.0f) return th;
-  if (C <= 0.0f) return 0.0f;
-  float r;
-  if (A == 0.0f) {
-    r = __fdividef(-C, Bq);
-  } else {
-    const float sq = sqrtf(fmaxf(fmaf(Bq, Bq, -4.0f * A * C), 0.0f));
-    const float Q = -0.5f * (Bq + copysignf(sq, Bq));
-    if (Q == 0.0f) return 0.0f;
-    const float r1q = __fdividef(Q, A), r2q = __fdividef(C, Q);
-    r = -1.0f;
-    if (r1q > 0.0f) r = r1q;
-    if (r2q > 0.0f && (r < 0.0f || r2q < r)) r = r2q;
-    if (r < 0.0f) return 0.0f;
-  }
-  return fminf(fmaxf(r, 0.0f), th);
+  const bool ok_th = fmaf(th, fmaf(th, A, Bq), C) >= 0.0f;
+  // the linear root (A = 0)
+  const float r_lin = __fdividef(-C, Bq);
+  // the quadratic's roots, the smallest positive one
+  const float sq = sqrtf(fmaxf(fmaf(Bq, Bq, -4.0f * A * C), 0.0f));
+  const float Q = -0.5f * (Bq + copysignf(sq, Bq));
+  const float r1q = __fdividef(Q, A), r2q = __fdividef(C, Q);
+  float r = r1q > 0.0f ? r1q : -1.0f;
+  r = (r2q > 0.0f && (r < 0.0f || r2q < r)) ? r2q : r;
+  const bool zero_q = Q == 0.0f || r < 0.0f;
+  const float rr = A == 0.0f ? r_lin : r;
+  const float root = fminf(fmaxf(rr, 0.0f), th);
+  return ok_th ? th : ((C <= 0.0f || (A != 0.0f && zero_q)) ? 0.0f : root);
 }
 
-// b holds the node's limits, computed once per node by node_p2.
 // theta = 1 admissible: V = U0 + D inside the density limits with
 // q(1) = rho E - |m|^2 / 2 - kk rho >= 0.
 __device__ __forceinline__ bool theta_one(const float4 U0, const float4 D, const Bnd b) {
