@@ -38,10 +38,10 @@ METRIC = "ensemble cell-updates/s (GLUPS) & % HBM roofline, mixed vs FP64, at st
 BYTES_PER_UPDATE = {"mixed": 160, "fp64": 320}
 # DRAM traffic of one step-kernel launch from an ncu capture, with the sha256
 # of the kernel source and the launch design it was taken on (reported as null
-# once either differs).  Mixed: 607.0 MB read + written for the 4.0 M
+# once either differs).  Mixed: 606.8 MB read + written for the 4.0 M
 # cell-updates of the M = 10 capture, scaled to 400 M cell-updates.
 NCU_TRAFFIC = {
-    "mixed": {"sha": "082260e3e440ed91", "design": "march30pf4w", "bytes_per_launch": 60.70e9,
+    "mixed": {"sha": "2afd2e9bafeaf439", "design": "march30pf4w", "bytes_per_launch": 60.68e9,
               "capture": "M=10, 400x200 + 800x400, scaled by cell-updates"},
 }
 

@@ -155,7 +155,7 @@ __device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float
 // theta = 1 is tested first, inline and without any division (theta_one, the
 // common case); the general case is a call.  The constants come by value so
 // that no context struct lives in local memory.
-__device__ __noinline__ float theta_star_general(const float4 U0, const float4 D, float lower, float hi_b,
+__device__ __forceinline__ float theta_star_general(const float4 U0, const float4 D, float lower, float hi_b,
                                                  float kk) {
   // every branch of the rule is evaluated and the taken one selected, so
   // the lanes of a warp that enter here stay converged
