@@ -156,11 +156,18 @@ class OraclePool:
         self.ex.shutdown()
 
 
+def horizon_of(args) -> str:
+    if args.t_final > 0:
+        return (f"to the next output time t_k = k x {args.dt_snap} (landing rule; a fresh ensemble after "
+                f"t = {args.t_final})")
+    return f"{args.solver_steps} VLBM steps"
+
+
 def workload_config(levels, M, horizon, prec):
     nxa = " + ".join(f"{nx}x{ny}" for nx, ny in levels)
     return {"workload": f"Mach 2000 jet ensemble, M={M} per GPU, levels {nxa} in one launch, {prec}, R-theta "
-                        f"limiter, per bench step: init + every realization {horizon} + density + "
-                        f"W1/mean/std statistics between the levels",
+                        f"limiter, per bench step: every realization {horizon} + density + W1/mean/std "
+                        f"statistics between the levels",
             "levels": levels, "M_per_gpu": M, "horizon": horizon, "precision": prec,
             "l2": "inputs larger than L2 (lattice state "
                   f"{sum(nx * ny for nx, ny in levels) * M * BYTES_PER_UPDATE[prec] / 1e9:.0f} GB)"}
@@ -192,8 +199,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox jet ensemble)",
         "impl": "reference",
-        "config": workload_config(levels, args.m, f"to t = {args.t_final} (landing rule)" if args.t_final > 0
-                                  else f"{args.solver_steps} VLBM steps", args.precision),
+        "config": workload_config(levels, args.m, horizon_of(args), args.precision),
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": pool.workers, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -224,7 +230,7 @@ def run_ours(args):
     prec = args.precision
     ens = vlbm.Ensemble(levels, precision=prec, stream=stream)
     m_begin = rank * M
-    horizon = f"to t = {args.t_final} (landing rule)" if args.t_final > 0 else f"{S} VLBM steps"
+    horizon = horizon_of(args)
     (nxa, nya), (nxb, nyb) = levels
     dens_a = torch.empty((M, nya, nxa), dtype=torch.float32, device=dev)
     dens_b = torch.empty((M, nyb, nxb), dtype=torch.float32, device=dev)
@@ -238,28 +244,33 @@ def run_ours(args):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     step_ms = []
 
-    def advance():
-        # the hot path of one bench step: every realization of both levels to
-        # the paper's final time (landing rule), or a fixed number of steps
-        if args.t_final > 0:
-            ens.advance_to(args.t_final)
-        else:
-            ens.step(S)
+    # A bench step advances every realization to the next of the paper's
+    # output times (every dt_snap up to t_final, landing rule) and takes the
+    # statistics between the levels there; after t_final the next step starts
+    # from a fresh ensemble.  A cycle of n_snap steps is one full run.
+    n_snap = max(1, int(round(args.t_final / args.dt_snap))) if args.t_final > 0 else 1
+    phase = {"k": n_snap}  # snapshot index of the state held (n_snap: start a new run)
 
-    def cells_done() -> int:
-        # cell-updates of the run just finished (realizations take different step counts)
-        return sum(nx * ny * int(ens.time(l)[1].sum()) for l, (nx, ny) in enumerate(levels))
+    def steps_now():
+        return [ens.time(l)[1].copy() for l in range(len(levels))]
 
     def bench_step(e2e: bool, timed: bool):
-        if e2e:
-            ens.init_samples(host_xi)
-        else:
-            ens.init(SEED, M, m_begin=m_begin)
+        if phase["k"] >= n_snap:
+            if e2e:
+                ens.init_samples(host_xi)
+            else:
+                ens.init(SEED, M, m_begin=m_begin)
+            phase["k"] = 0
+        before = steps_now() if phase["k"] > 0 else [np.zeros(M, dtype=np.int64) for _ in levels]
         if timed:
             ev[0].record(stream)
-        advance()
+        if args.t_final > 0:
+            ens.advance_to(args.t_final * (phase["k"] + 1) / n_snap)
+        else:
+            ens.step(S)
         if timed:
             ev[1].record(stream)
+        phase["k"] += 1
         ens.density(0, out=dens_a)
         ens.density(1, out=dens_b)
         if dist is None:
@@ -271,7 +282,8 @@ def run_ours(args):
             for h, k in zip(host_out, ("mean_a", "std_a", "mean_b", "std_b", "w1")):
                 h.copy_(st[k], non_blocking=True)
             stream.synchronize()  # the caller reads the statistics of this step
-        return st
+        after = steps_now()
+        return sum(nx * ny * int((a - b).sum()) for (nx, ny), a, b in zip(levels, after, before))
 
     def barrier():
         torch.cuda.synchronize()
@@ -281,18 +293,16 @@ def run_ours(args):
     def timed_loop(e2e: bool, warmup: int):
         for _ in range(warmup):
             bench_step(e2e, False)
-        # every bench step repeats the same inputs: its cell-updates are those of the warm-up
-        cells = cells_done()
         barrier()
         launches0 = vlbm.kernel_launches()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         h0 = time.perf_counter()
         t0.record(stream)
+        cells = 0
         for _ in range(args.steps):
-            bench_step(e2e, not e2e)
+            cells += bench_step(e2e, not e2e)
             if not e2e:
-                torch.cuda.synchronize()
                 step_ms.append(ev[0].elapsed_time(ev[1]))
         t1.record(stream)
         barrier()
@@ -311,12 +321,11 @@ def run_ours(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms, launches, cells_step, cells_all = timed_loop(False, args.warmup)
+    ms, launches, cells_timed, cells_all = timed_loop(False, args.warmup)
     clk = clocks.stop()
     # the system is warm: one untimed end-to-end step, then the timed ones
+    phase["k"] = n_snap
     ms_e2e, _, _, cells_all_e2e = timed_loop(True, 1)
-    run_steps = {f"{nx}x{ny}": [int(ens.time(l)[1].min()), int(ens.time(l)[1].max())]
-                 for l, (nx, ny) in enumerate(levels)}
     design = ens.step_design()
 
     # the FP64 path on the same levels, fewer realizations (rate per cell update)
@@ -359,13 +368,14 @@ def run_ours(args):
         ens_m.close()
         ens_d.close()
 
-    value = cells_all * args.steps / (ms / 1e3) / 1e9
-    e2e_value = cells_all_e2e * args.steps / (ms_e2e / 1e3) / 1e9
+    value = cells_all / (ms / 1e3) / 1e9
+    e2e_value = cells_all_e2e / (ms_e2e / 1e3) / 1e9
     hbm, src = peaks()
-    # the step kernels of one bench step: algorithmic bytes of its cell-updates
-    # over the CUDA-event time of the whole advance (ticks, landing included)
-    adv_s = float(np.mean(step_ms)) / 1e3
-    achieved = BYTES_PER_UPDATE[prec] * cells_step / adv_s / 1e9
+    # the step kernels of the timed bench steps: algorithmic bytes of their
+    # cell-updates over the CUDA-event time of the advances (ticks, landing
+    # and the polling of active realizations included)
+    adv_s = float(np.sum(step_ms)) / 1e3
+    achieved = BYTES_PER_UPDATE[prec] * cells_timed / adv_s / 1e9
     sha = kernel_sha(prec)
     tr = NCU_TRAFFIC.get(prec)
     traffic = tr["bytes_per_launch"] if tr and tr["sha"] == sha and tr["design"] == design[1] else None
@@ -385,17 +395,17 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
             "data": "synthetic (seeded Philox4x32-10 Karhunen-Loeve jet inlets)",
-            "config": {**workload_config(levels, M, horizon, prec), "steps_per_realization": run_steps,
-                       "cell_updates_per_step": cells_step},
+            "config": {**workload_config(levels, M, horizon, prec), "snapshots_per_run": n_snap,
+                       "cell_updates_timed": cells_timed},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": f"step_{prec}_kernel", "design": design[1], "peak_source": f"{src} hbm_gbs",
                          "bytes_per_cell_update": BYTES_PER_UPDATE[prec],
                          "advance_ms": adv_s * 1e3,
-                         "note": "achieved = 160 B x cell-updates of one bench step / CUDA-event time of its "
-                                 "advance (every step launch, tick and landing check; realizations that "
-                                 "landed leave the launches); traffic: ncu DRAM bytes of one launch with "
-                                 "every realization active"},
+                         "note": "achieved = 160 B x cell-updates of the timed bench steps / CUDA-event time "
+                                 "of their advances (every step launch, tick and landing check; realizations "
+                                 "that landed leave the launches); traffic: ncu DRAM bytes of one launch "
+                                 "with every realization active"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": M * 2 * K * 8,
                     "d2h_bytes_per_step": 5 * nxa * nya * 8,
@@ -417,14 +427,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=7)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--m", type=int, default=M_PER_GPU)
     ap.add_argument("--solver-steps", type=int, default=64,
                     help="fixed steps per bench step when --t-final is 0; the statistic-error check's horizon")
-    ap.add_argument("--t-final", type=float, default=0.0035, help="advance every realization to this time")
+    ap.add_argument("--t-final", type=float, default=0.0035, help="the run's final time (0: fixed steps)")
+    ap.add_argument("--dt-snap", type=float, default=0.0005, help="output interval: one bench step per output time")
     ap.add_argument("--fp64-m", type=int, default=50)
     ap.add_argument("--fp64-steps", type=int, default=8)
     ap.add_argument("--stat-m", type=int, default=16)
