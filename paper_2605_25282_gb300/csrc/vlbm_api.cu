@@ -1,5 +1,8 @@
 // Host side of the C ABI declared in include/vlbm.h: validation, device
-// memory, the per-step launch sequence and its CUDA-graph capture, I/O.
+// memory, the per-step launch sequence and its CUDA-graph capture, I/O, the
+// statistics entry points, and the checkpointed gradient driver
+// (vlbm_grad_amplitudes: forward with checkpoints, then the reverse sweep of
+// the adjoint kernels window by window).
 //
 // One step of the ensemble is two launches on the context stream:
 //   step kernel  (every level, realization and tile in one grid)
@@ -19,21 +22,6 @@
 
 #include "vlbm_internal.cuh"
 
-namespace vlbm {
-size_t functional_scratch_doubles(int M);
-int noalloc_max_m();
-cudaError_t noalloc_scratch(double** out);
-int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why);
-cudaError_t functional_launch(const void* a, int a_f32, int nxa, int nya, const void* b, int b_f32, int nxb, int M,
-                              double* scratch, double* out, cudaStream_t s);
-int quantile_launch(const void* ens, int f32, int nx, int ny, int M, const double* probs, int nprob, double* out,
-                    cudaStream_t s, const char** why);
-int histogram_launch(const void* ens, int f32, int nx, int ny, int M, const double* edges, int nbins, double* out,
-                     cudaStream_t s, const char** why);
-int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32, int nxb,
-                 int nyb, int M, double* mean_a, double* std_a, double* mean_b, double* std_b, double* w1,
-                 cudaStream_t s, const char** why);
-}  // namespace vlbm
 
 using namespace vlbm;
 

@@ -9,6 +9,8 @@
 //                     dt = dx / a_n (Sec. 2.3), landing on t*, and the advance of
 //                     t, step count and lambda after a step.
 //  - moments / density / get_state / set_state: layout conversions.
+//  - bounded_wait_probe: one mbarrier wait that nothing completes, bounded
+//    like the step kernels' waits (the failure-detection check).
 #include <cmath>
 
 #include "vlbm_internal.cuh"

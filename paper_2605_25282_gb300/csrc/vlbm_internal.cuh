@@ -130,6 +130,22 @@ cudaError_t launch_step_mixed(const Launch& L, int variant, cudaStream_t s);
 cudaError_t restrict_launch(const void* ens, int is_f32, int nx, int ny, int M, int r, void* out, int out_f32,
                             cudaStream_t s);
 
+// Statistics launchers (vlbm_stats.cu, vlbm_diag.cu); the int-returning ones
+// report a status code and, on failure, a reason in *why.
+size_t functional_scratch_doubles(int M);
+int noalloc_max_m();
+cudaError_t noalloc_scratch(double** out);
+int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why);
+cudaError_t functional_launch(const void* a, int a_f32, int nxa, int nya, const void* b, int b_f32, int nxb, int M,
+                              double* scratch, double* out, cudaStream_t s);
+int quantile_launch(const void* ens, int f32, int nx, int ny, int M, const double* probs, int nprob, double* out,
+                    cudaStream_t s, const char** why);
+int histogram_launch(const void* ens, int f32, int nx, int ny, int M, const double* edges, int nbins, double* out,
+                     cudaStream_t s, const char** why);
+int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b, int b_is_f32, int nxb,
+                 int nyb, int M, double* mean_a, double* std_a, double* mean_b, double* std_b, double* w1,
+                 cudaStream_t s, const char** why);
+
 // Two-point Wasserstein distance (vlbm_w12.cu): per-pair values into pair_w
 // [npd^4] and their mean into *out (device).  Dynamic shared memory per CTA:
 size_t w12_smem_bytes(int M);

@@ -9,6 +9,9 @@
 //   W1   = sum_m |a_(m) - b_(m)| / M  over the ascending order statistics.
 // The gather is strided by the field size; consecutive CTAs are neighbouring
 // cells, so the rest of each 32-byte sector is reused from L2.
+// restrict_kernel applies the restriction alone (one thread per coarse cell
+// and realization, the same summation order), for comparisons of several
+// levels on one common grid.
 #include "vlbm_internal.cuh"
 
 namespace vlbm {
