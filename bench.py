@@ -44,6 +44,17 @@ NCU_TRAFFIC = {
     "mixed": {"sha": "2afd2e9bafeaf439", "design": "march30pf4w", "bytes_per_launch": 60.68e9,
               "capture": "M=10, 400x200 + 800x400, scaled by cell-updates"},
 }
+# The FP64 step kernel is bound by the FP64 pipe, not by HBM.  ncu counters of
+# one launch (M = 2, 400x200 + 800x400, 800,000 cell-updates), with the sha256
+# of the kernel source and of its math header: FP64-pipe warp instructions x 32
+# per cell-update (every FP64 add, multiply, fused multiply-add, compare,
+# min/max and conversion; an upper bound where lanes idle), and the FLOPs of
+# its adds, multiplies and fused multiply-adds (161.5 M DADD + 207.8 M DMUL +
+# 129.5 M DFMA thread instructions).  GB300 issues 2 FP64 thread operations per
+# SM and clock.
+FP64_ALU = {"sha": "72c2b9ea2d4f61d6+d4e76c39de7e1da7", "pipe_inst_per_update": 18172822 * 32 / 800000,
+            "flop_per_update": (161525984 + 207834288 + 2 * 129468696) / 800000, "ops_per_sm_clock": 2,
+            "sms": 152}
 
 
 def peaks():
@@ -56,9 +67,35 @@ def peaks():
 
 
 def kernel_sha(precision: str) -> str:
-    name = "vlbm_step_mixed.cu" if precision == "mixed" else "vlbm_step_f64.cu"
-    with open(os.path.join(HERE, "paper_2605_25282_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    names = ["vlbm_step_mixed.cu"] if precision == "mixed" else ["vlbm_step_f64.cu", "vlbm_f64_math.cuh"]
+    out = []
+    for name in names:
+        with open(os.path.join(HERE, "paper_2605_25282_gb300", "csrc", name), "rb") as f:
+            out.append(hashlib.sha256(f.read()).hexdigest()[:16])
+    return "+".join(out)
+
+
+def sm_max_mhz() -> float:
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
+def fp64_alu(glups: float):
+    """ALU roofline of the FP64 step kernel at `glups` G cell-updates/s (None
+    once the kernel source differs from the one the counters were taken on)."""
+    if kernel_sha("fp64") != FP64_ALU["sha"]:
+        return None
+    mhz = sm_max_mhz()
+    peak = FP64_ALU["sms"] * FP64_ALU["ops_per_sm_clock"] * mhz * 1e6 / 1e9
+    achieved = glups * FP64_ALU["pipe_inst_per_update"]
+    return {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "G FP64 inst/s",
+            "frac": achieved / peak, "inst_per_cell_update": FP64_ALU["pipe_inst_per_update"],
+            "flop_per_cell_update": FP64_ALU["flop_per_update"],
+            "peak_source": f"{FP64_ALU['sms']} SMs x {FP64_ALU['ops_per_sm_clock']} FP64 ops per clock x "
+                           f"{mhz:.0f} MHz (sm_max_mhz)"}
 
 
 class ClockSampler:
@@ -165,12 +202,13 @@ def horizon_of(args) -> str:
 
 def workload_config(levels, M, horizon, prec):
     nxa = " + ".join(f"{nx}x{ny}" for nx, ny in levels)
+    state_gb = sum(nx * ny for nx, ny in levels) * M * BYTES_PER_UPDATE[prec] / 1e9
     return {"workload": f"Mach 2000 jet ensemble, M={M} per GPU, levels {nxa} in one launch, {prec}, R-theta "
                         f"limiter, per bench step: every realization {horizon} + density + W1/mean/std "
                         f"statistics between the levels",
             "levels": levels, "M_per_gpu": M, "horizon": horizon, "precision": prec,
-            "l2": "inputs larger than L2 (lattice state "
-                  f"{sum(nx * ny for nx, ny in levels) * M * BYTES_PER_UPDATE[prec] / 1e9:.0f} GB)"}
+            "l2": f"inputs {'larger' if state_gb > 0.129 else 'SMALLER'} than L2 (lattice state "
+                  f"{state_gb:.3g} GB)"}
 
 
 def run_reference(args):
@@ -345,7 +383,7 @@ def run_ours(args):
         r64 = c64 / t64 / 1e9
         hbm, src = peaks()
         fp64 = {"value": r64, "unit": "GLUPS", "M": args.fp64_m, "solver_steps": args.fp64_steps,
-                "hbm_frac": r64 * 1e9 * BYTES_PER_UPDATE["fp64"] / (hbm * 1e9)}
+                "hbm_frac": r64 * 1e9 * BYTES_PER_UPDATE["fp64"] / (hbm * 1e9), "alu": fp64_alu(r64)}
         e64.close()
 
     # error of every statistic of the mixed path against the FP64 path (whose
@@ -379,6 +417,26 @@ def run_ours(args):
     sha = kernel_sha(prec)
     tr = NCU_TRAFFIC.get(prec)
     traffic = tr["bytes_per_launch"] if tr and tr["sha"] == sha and tr["design"] == design[1] else None
+    if prec == "mixed":
+        kname = {"tile": "step_mixed_tile_kernel", "pers": "step_mixed_persistent_kernel",
+                 "marc": "step_mixed_march_kernel"}.get(design[1][:4], "step_mixed_kernel")
+    else:
+        kname = "step_f64_kernel"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "kernel": kname, "design": design[1], "peak_source": f"{src} hbm_gbs",
+                "bytes_per_cell_update": BYTES_PER_UPDATE[prec],
+                "advance_ms": adv_s * 1e3,
+                "note": f"achieved = {BYTES_PER_UPDATE[prec]} B x cell-updates of the timed bench steps / "
+                        "CUDA-event time of their advances (every step launch, tick and landing check; "
+                        "realizations that landed leave the launches); traffic: ncu DRAM bytes of one launch "
+                        "with every realization active"}
+    if prec == "fp64":
+        # bound by the FP64 pipe: the roofline is the ALU one, the HBM figures stay beside it
+        alu = fp64_alu(cells_timed / adv_s / 1e9)
+        if alu is not None:
+            roofline = {**alu, "kernel": kname, "design": design[1], "advance_ms": adv_s * 1e3,
+                        "hbm": {"achieved_gbs": achieved, "frac": achieved / hbm, "traffic": traffic}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -397,15 +455,7 @@ def run_ours(args):
             "data": "synthetic (seeded Philox4x32-10 Karhunen-Loeve jet inlets)",
             "config": {**workload_config(levels, M, horizon, prec), "snapshots_per_run": n_snap,
                        "cell_updates_timed": cells_timed},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": f"step_{prec}_kernel", "design": design[1], "peak_source": f"{src} hbm_gbs",
-                         "bytes_per_cell_update": BYTES_PER_UPDATE[prec],
-                         "advance_ms": adv_s * 1e3,
-                         "note": "achieved = 160 B x cell-updates of the timed bench steps / CUDA-event time "
-                                 "of their advances (every step launch, tick and landing check; realizations "
-                                 "that landed leave the launches); traffic: ncu DRAM bytes of one launch "
-                                 "with every realization active"},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": M * 2 * K * 8,
                     "d2h_bytes_per_step": 5 * nxa * nya * 8,
