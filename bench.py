@@ -279,8 +279,9 @@ def run_ours(args):
     rng = np.random.default_rng(SEED + rank)
     host_xi = torch.from_numpy(rng.uniform(-1.0, 1.0, (M, 2 * K))).pin_memory()
 
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     step_ms = []
+    stats_ms = []
 
     # A bench step advances every realization to the next of the paper's
     # output times (every dt_snap up to t_final, landing rule) and takes the
@@ -311,11 +312,15 @@ def run_ours(args):
         phase["k"] += 1
         ens.density(0, out=dens_a)
         ens.density(1, out=dens_b)
+        if timed:
+            ev[2].record(stream)
         if dist is None:
             st = vlbm.stats_w1_mean_std(dens_a, dens_b, stream=stream)
         else:
             # statistics over the realizations of every rank: one row-block all-to-all
             st = sharded.gpu_statistics(dens_a, dens_b)
+        if timed:
+            ev[3].record(stream)
         if e2e:
             for h, k in zip(host_out, ("mean_a", "std_a", "mean_b", "std_b", "w1")):
                 h.copy_(st[k], non_blocking=True)
@@ -342,6 +347,7 @@ def run_ours(args):
             cells += bench_step(e2e, not e2e)
             if not e2e:
                 step_ms.append(ev[0].elapsed_time(ev[1]))
+                stats_ms.append(ev[2].elapsed_time(ev[3]))
         t1.record(stream)
         barrier()
         # device time for the kernel-only figure; host wall time end to end
@@ -431,6 +437,19 @@ def run_ours(args):
                         "CUDA-event time of their advances (every step launch, tick and landing check; "
                         "realizations that landed leave the launches); traffic: ncu DRAM bytes of one launch "
                         "with every realization active"}
+    # the statistics call of each timed step (restriction of the fine level,
+    # per-cell mean, std and sorted W1): read (1 + r^2) M FP32 samples and
+    # write 5 FP64 fields per coarse cell
+    r = nxb // nxa
+    # (one GPU; sharded, the call also restricts, exchanges and gathers)
+    stats_bytes = nxa * nya * (M * 4 * (1 + r * r) + 5 * 8) if dist is None else None
+    stats_s = float(np.mean(stats_ms)) / 1e3
+    stats_gbs = stats_bytes / stats_s / 1e9 if stats_bytes else None
+    stats = {"kernel": "stats_kernel", "ms_per_call": stats_s * 1e3, "bytes_per_call": stats_bytes,
+             "achieved_gbs": stats_gbs, "hbm_frac": stats_gbs / hbm if stats_gbs else None,
+             "share_of_step": stats_s * 1e3 / (ms / args.steps),
+             "bound": "on-chip sort (two bitonic sorts of the cell's samples in shared memory)",
+             "sharded": dist is not None}
     if prec == "fp64":
         # bound by the FP64 pipe: the roofline is the ALU one, the HBM figures stay beside it
         alu = fp64_alu(cells_timed / adv_s / 1e9)
@@ -464,6 +483,7 @@ def run_ours(args):
                             "advances, and reads the statistics back to pinned host memory"},
             "gpu_launches": launches,
             "clocks": clk,
+            "stats": stats,
             "fp64_path": fp64,
             "stat_error": stat_err,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
