@@ -145,11 +145,14 @@ class ClockSampler:
 
 
 def dist_setup(gpus: int):
+    """Rank, world size and local GPU from the launcher's environment (one
+    process per GPU under torchrun; without it a single rank).  The world size
+    is the launcher's: --gpus N without torchrun runs and reports one GPU."""
     rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    world = max(int(os.environ.get("WORLD_SIZE", "1")), 1)
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world != gpus:
-        world = max(world, 1)
+    if world != gpus and rank == 0:
+        print(f"bench: --gpus {gpus} but {world} process(es) launched; reporting {world}", file=sys.stderr)
     return rank, world, local
 
 
