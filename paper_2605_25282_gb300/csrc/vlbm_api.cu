@@ -308,6 +308,10 @@ int init_impl(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb
   if (perturb) P = *perturb;
   if (P.K < 0 || P.K > kMaxModes) return fail(c, VLBM_EINVAL, "K must be in [0, 16]");
   if (!(P.r_jet > 0.0)) return fail(c, VLBM_EINVAL, "r_jet must be > 0");
+  // from here on the context's state changes: until this call completes it
+  // holds no ensemble (a failure below leaves VLBM_ESTATE for the next call)
+  c->initialized = false;
+  c->prepared = false;
   if (c->M != M || c->mem.empty()) {
     release_levels(c);
     c->mem.resize(c->grids.size());
@@ -328,7 +332,6 @@ int init_impl(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb
       if (!mm.lat || !mm.inlet || !mm.inlet_f || !mm.rs) {
         release_levels(c);
         c->M = 0;
-        c->initialized = false;
         return fail(c, VLBM_ENOMEM,
                     "device allocation of " + std::to_string(mm.lat_bytes) + " bytes for level " +
                         std::to_string(l) + " failed");
@@ -336,7 +339,11 @@ int init_impl(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb
     }
     if (!c->d_count) {
       c->d_count = static_cast<int*>(dev_alloc(c, sizeof(int)));
-      if (!c->d_count) return fail(c, VLBM_ENOMEM, "device allocation failed");
+      if (!c->d_count) {
+        release_levels(c);
+        c->M = 0;
+        return fail(c, VLBM_ENOMEM, "device allocation of the active-realization counter failed");
+      }
     }
     c->M = M;
   }
