@@ -277,7 +277,13 @@ int stats_histogram(const void* ens, int is_f32, int nx, int ny, int M, const do
  * step counts, kinetic-speed bookkeeping) to host memory.  With host_buf NULL,
  * *bytes receives the size needed.  Synchronises the stream.  Restoring with
  * vlbm_load into a context created with the same levels, precision and M
- * resumes bit-identically. */
+ * resumes bit-identically.  vlbm_load needs an initialised context (its
+ * device memory is reused) and returns VLBM_EINVAL when the header (format,
+ * precision, level count, M) or the size does not match.  The KL uniforms and
+ * amplitudes that vlbm_grad_amplitudes differentiates with respect to are not
+ * part of the checkpoint: they stay those of the context's last
+ * vlbm_init_ensemble* call.  vlbm_save returns the sticky realization flags
+ * (VLBM_ENONPOSITIVE ...) after a complete save. */
 int vlbm_save(vlbm_ctx* ctx, void* host_buf, size_t* bytes);
 int vlbm_load(vlbm_ctx* ctx, const void* host_buf, size_t bytes);
 

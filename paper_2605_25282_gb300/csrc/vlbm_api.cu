@@ -595,6 +595,7 @@ int vlbm_time(vlbm_ctx* c, int level, double* t_host, long long* steps_host) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
   std::vector<RealState> h;
   st = read_flags(c, level, &h);
+  if (h.size() != (size_t)c->M) return st;  // the device read itself failed
   for (int m = 0; m < c->M; ++m) {
     if (t_host) t_host[m] = h[m].t;
     if (steps_host) steps_host[m] = h[m].steps;
