@@ -263,7 +263,7 @@ int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why
     *why = "need nxa, nya >= 1 and 1 <= M <= 4096";
     return VLBM_EINVAL;
   }
-  if (nxb % nxa != 0 || nyb % nya != 0 || nxb / nxa != nyb / nya) {
+  if (nxb < nxa || nyb < nya || nxb % nxa != 0 || nyb % nya != 0 || nxb / nxa != nyb / nya) {
     *why = "ensemble b must be an integer refinement (same factor in x and y) of ensemble a";
     return VLBM_EINVAL;
   }

@@ -124,7 +124,11 @@ int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* 
     *why = "need nxa, nya >= 1 and 1 <= M <= 4096";
     return VLBM_EINVAL;
   }
-  if (nxb % nxa != 0 || nyb % nya != 0 || nxb / nxa != nyb / nya) {
+  if ((long long)nxa * nya > 0x7fffffffLL) {
+    *why = "the coarse grid has more than 2^31 - 1 cells";
+    return VLBM_EINVAL;
+  }
+  if (nxb < nxa || nyb < nya || nxb % nxa != 0 || nyb % nya != 0 || nxb / nxa != nyb / nya) {
     *why = "ensemble b must be an integer refinement (same factor in x and y) of ensemble a";
     return VLBM_EINVAL;
   }

@@ -78,6 +78,12 @@ def test_stats_rejects_bad_shapes_without_launching():
     assert code == 1 and "M" in lib.vlbm_last_error(None).decode()
     code = lib.stats_w1_mean_std(None, 0, 10, 10, dummy, 0, 10, 10, 4, None, None, None, None, None, None)
     assert code == 1
+    # an empty fine level (refinement factor 0) and a coarse grid beyond one launch
+    code = lib.stats_w1_mean_std(dummy, 0, 10, 10, dummy, 0, 0, 0, 4, None, None, None, None, None, None)
+    assert code == 1 and "refinement" in lib.vlbm_last_error(None).decode()
+    code = lib.stats_w1_mean_std(dummy, 0, 65536, 65536, dummy, 0, 65536, 65536, 4, None, None, None, None, None,
+                                 None)
+    assert code == 1 and "2^31" in lib.vlbm_last_error(None).decode()
 
 
 def test_null_context_calls_fail_cleanly():
