@@ -472,6 +472,8 @@ int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_p
   vlbm_relax R;
   vlbm_default_relax(&R);
   if (relax) R = *relax;
+  for (double v : {R.alpha, R.kappa, R.rlmp_rel, R.rlmp_abs, R.eps_pos})
+    if (!std::isfinite(v)) return fail(nullptr, VLBM_EINVAL, "relaxation parameters must be finite");
   if (!(R.alpha >= 0.0 && R.alpha < 1.0)) return fail(nullptr, VLBM_EINVAL, "alpha must be in [0, 1)");
   if (!(R.kappa >= 1.0)) return fail(nullptr, VLBM_EINVAL, "kappa must be >= 1 (Bouchut bound)");
   if (R.limiter < 0 || R.limiter > 2) return fail(nullptr, VLBM_EINVAL, "unknown limiter");
@@ -481,6 +483,8 @@ int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_p
     const vlbm_grid& g = levels[l];
     if (g.nx < 3 || g.ny < 3) return fail(nullptr, VLBM_EINVAL, "every level needs nx, ny >= 3");
     if ((long long)g.nx * g.ny > (1LL << 31)) return fail(nullptr, VLBM_EINVAL, "level too large");
+    if (!std::isfinite(g.x_max) || !std::isfinite(g.y_min) || !std::isfinite(g.y_max))
+      return fail(nullptr, VLBM_EINVAL, "grid extents must be finite");
     if (!(g.x_max > 0) || !(g.y_max > g.y_min)) return fail(nullptr, VLBM_EINVAL, "empty domain");
     const double dx = g.x_max / g.nx, dy = (g.y_max - g.y_min) / g.ny;
     if (std::fabs(dx - dy) > 1e-12 * dx) return fail(nullptr, VLBM_EINVAL, "cells must be square");

@@ -59,6 +59,9 @@ def _create(levels, gamma=5 / 3, jet=None, amb=None, relax=None, precision=0):
     (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(1.0, 1.0, 2, 0.1, 0.0, 1e-13)), "alpha"),
     (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(0.0, 0.5, 2, 0.1, 0.0, 1e-13)), "kappa"),
     (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(0.0, 1.0, 5, 0.1, 0.0, 1e-13)), "limiter"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(0.0, float("inf"), 2, 0.1, 0.0, 1e-13)), "finite"),
+    (dict(levels=[vlbm.jet_grid(200, 100)], relax=vlbm.Relax(0.0, 1.0, 2, float("inf"), 0.0, 1e-13)), "finite"),
+    (dict(levels=[vlbm.Grid(200, 100, float("inf"), -0.625, 0.625)]), "finite"),
 ])
 def test_create_rejects_invalid_problems(case, expect):
     code, msg = _create(**case)
