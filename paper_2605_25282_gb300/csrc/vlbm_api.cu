@@ -307,7 +307,12 @@ int init_impl(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb
   vlbm_default_perturb(&P);
   if (perturb) P = *perturb;
   if (P.K < 0 || P.K > kMaxModes) return fail(c, VLBM_EINVAL, "K must be in [0, 16]");
-  if (!(P.r_jet > 0.0)) return fail(c, VLBM_EINVAL, "r_jet must be > 0");
+  if (!(P.r_jet > 0.0) || !std::isfinite(P.r_jet)) return fail(c, VLBM_EINVAL, "r_jet must be finite and > 0");
+  if (!std::isfinite(P.A) || !std::isfinite(P.p_decay))
+    return fail(c, VLBM_EINVAL, "the perturbation amplitude A and decay p must be finite");
+  if (P.use_amp)
+    for (int k = 0; k < P.K; ++k)
+      if (!std::isfinite(P.amp[k])) return fail(c, VLBM_EINVAL, "amp[" + std::to_string(k) + "] is not finite");
   // from here on the context's state changes: until this call completes it
   // holds no ensemble (a failure below leaves VLBM_ESTATE for the next call)
   c->initialized = false;

@@ -149,3 +149,41 @@ def test_allocation_failure_is_reported_without_device_work():
         assert lib.vlbm_step(ctx, 1) == 7  # VLBM_ESTATE: nothing initialised
     finally:
         lib.vlbm_destroy(ctx)
+
+
+@pytest.mark.parametrize("field, value, expect", [
+    ("A", float("inf"), "finite"),
+    ("p_decay", float("nan"), "finite"),
+    ("r_jet", float("inf"), "r_jet"),
+    ("r_jet", 0.0, "r_jet"),
+    ("amp", float("nan"), "amp[2]"),
+])
+def test_init_rejects_invalid_perturbations_before_device_work(field, value, expect):
+    lib = vlbm.load_library()
+    arr = (vlbm.Grid * 1)(vlbm.jet_grid(16, 8))
+    jet, amb = vlbm.Prim(5.0, 800.0, 0.0, 0.4127), vlbm.Prim(0.5, 0.0, 0.0, 0.4127)
+    calls = []
+
+    def refuse(nbytes, user):
+        calls.append(nbytes)
+        return None
+
+    alloc_cb, free_cb = vlbm.ALLOC_FN(refuse), vlbm.FREE_FN(lambda ptr, user: None)
+    ctx = ctypes.c_void_p()
+    # stream handle 1 is the legacy default stream: valid everywhere, no work enqueued here
+    assert lib.vlbm_create(arr, 1, 5 / 3, ctypes.byref(jet), ctypes.byref(amb), None, 1, ctypes.c_void_p(1),
+                           alloc_cb, free_cb, None, ctypes.byref(ctx)) == 0
+    try:
+        p = vlbm.PerturbParams(K=4).c()
+        if field == "amp":
+            p.use_amp = 1
+            for k in range(4):
+                p.amp[k] = 0.01
+            p.amp[2] = value
+        else:
+            setattr(p, field, value)
+        code = lib.vlbm_init_ensemble(ctx, 0, 2, ctypes.byref(p))
+        assert code == 1 and expect in lib.vlbm_last_error(ctx).decode(), (code, lib.vlbm_last_error(ctx))
+        assert calls == []  # rejected before any allocation
+    finally:
+        lib.vlbm_destroy(ctx)
