@@ -49,6 +49,19 @@ def test_w1_equals_cdf_integral_and_handles_ties():
                 assert abs(w1[j, i] - w1_cdf(a[:, j, i], b[:, j, i])) < 1e-12
 
 
+def test_w1_equals_library_wasserstein_at_ensemble_size():
+    # an independent implementation (scipy's CDF-based distance) at the
+    # ensemble size of the batched runs, M = 1000
+    stats = pytest.importorskip("scipy.stats")
+    a = inputs.random_samples(11, 1000, 2, 3)
+    b = inputs.random_samples(12, 1000, 2, 3)
+    *_, w1 = O.ensemble_stats(a, b)
+    for j in range(2):
+        for i in range(3):
+            want = stats.wasserstein_distance(a[:, j, i], b[:, j, i])
+            assert abs(w1[j, i] - want) <= 1e-12 * max(1.0, abs(want))
+
+
 def test_w1_metric_properties():
     a = inputs.random_samples(3, 50, 2, 2)
     b = inputs.random_samples(4, 50, 2, 2)
