@@ -14,7 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 import torch
@@ -145,7 +145,7 @@ def jet_grid(nx: int, ny: int, x_max: float = 2.5) -> Grid:
     return Grid(nx, ny, x_max, -0.5 * ny * dx, 0.5 * ny * dx)
 
 
-@dataclass
+@dataclass(frozen=True)
 class JetProblem:
     """Sec. 2.2 constants of the Mach 2000 jet."""
     gamma: float = 5.0 / 3.0
@@ -155,7 +155,7 @@ class JetProblem:
     rho_amb: float = 0.5
 
 
-@dataclass
+@dataclass(frozen=True)
 class PerturbParams:
     """Sec. 2.3, Eq. (karhunenExp)."""
     r_jet: float = 0.05
@@ -174,7 +174,7 @@ class PerturbParams:
         return p
 
 
-@dataclass
+@dataclass(frozen=True)
 class RelaxParams:
     alpha: float = 0.0
     kappa: float = 1.0

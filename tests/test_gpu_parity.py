@@ -10,7 +10,6 @@ import pytest
 import torch
 
 from oracle import oracle as O
-from paper_2605_25282_gb300 import vlbm
 from tests import gpu_helpers as H
 from tests import inputs
 

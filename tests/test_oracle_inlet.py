@@ -9,7 +9,6 @@ envelope the paper prints in Fig. 1.
 import os
 
 import numpy as np
-import pytest
 
 from oracle import oracle as O
 
