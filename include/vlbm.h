@@ -110,8 +110,9 @@ typedef void (*vlbm_free_fn)(void* ptr, void* user);
 void vlbm_default_relax(vlbm_relax* relax);
 void vlbm_default_perturb(vlbm_perturb* perturb);
 
-/* Sec. 2.1-2.2: validates the problem (grids, gamma > 1, states with
- * rho, p > 0) and creates a context.  Several levels (e.g. the refinement
+/* Sec. 2.1-2.2: validates the problem (grids with finite extents and square
+ * cells, gamma > 1, finite states with rho, p > 0, finite relaxation
+ * parameters in range; VLBM_EINVAL otherwise) and creates a context.  Several levels (e.g. the refinement
  * ladder of Sec. 3.3) advance together in every call.  cuda_stream may be
  * NULL: the context then creates and owns a non-blocking stream (at the
  * first initialising call).  alloc/free may be NULL (cudaMalloc/cudaFree).
@@ -124,7 +125,12 @@ int vlbm_create(const vlbm_grid* levels, int nlevels, double gamma, const vlbm_p
  * of M realizations on every level (re-allocates if M changes), draws the inlet
  * density of realization m = 0..M-1, sets the initial condition with
  * equilibrium populations and resets t = 0, steps = 0.  perturb may be NULL
- * (defaults).  Realization m is identical for every M > m (nested prefixes). */
+ * (defaults).  Realization m is identical for every M > m (nested prefixes).
+ * Invalid arguments (M outside [1, 65535], K > 16, r_jet <= 0, non-finite A,
+ * p_decay or amp[k]) return VLBM_EINVAL and leave an existing ensemble as it
+ * was; a failure after that (allocation: VLBM_ENOMEM, a launch: VLBM_ECUDA)
+ * leaves the context without an ensemble, so that stepping calls return
+ * VLBM_ESTATE until an initialisation succeeds. */
 int vlbm_init_ensemble(vlbm_ctx* ctx, uint64_t seed, int M, const vlbm_perturb* perturb);
 
 /* As vlbm_init_ensemble, for the block of realizations m_begin..m_begin+M-1
@@ -193,8 +199,9 @@ int vlbm_set_state(vlbm_ctx* ctx, int level, int m0, int count, const double* u,
  * each realization of b is first block-averaged onto a's grid.  Outputs
  * (device, FP64, [nya][nxa], any may be NULL): mean and population std of a and
  * of the restricted b, and the one-point W1 = (1/M) sum_m |a_(m) - b_(m)| over
- * the ascending order statistics.  1 <= M <= 4096.  Asynchronous on
- * cuda_stream (may be NULL). */
+ * the ascending order statistics.  1 <= M <= 4096, nxa nya < 2^31; a b that
+ * is not an integer refinement of a (same factor in x and y) is VLBM_EINVAL.
+ * Asynchronous on cuda_stream (may be NULL). */
 int stats_w1_mean_std(const void* ens_a, int a_is_f32, int nxa, int nya, const void* ens_b,
                       int b_is_f32, int nxb, int nyb, int M, double* mean_a, double* std_a,
                       double* mean_b, double* std_b, double* w1, void* cuda_stream);
