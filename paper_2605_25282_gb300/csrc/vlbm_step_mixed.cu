@@ -41,10 +41,12 @@ namespace {
 
 constexpr int TX = 32;
 
-// Limits of theta_star at a node: density floor and ceiling, and the pressure
-// floor as kk = eps_p / (gamma - 1).
+// Limits of theta_star at a node with first-order state U: room below and
+// above its density bounds (rho_LF - lower bound, upper bound - rho_LF, both
+// >= 0), its energy less the pressure floor Ek = E_LF - eps_p / (gamma - 1),
+// and the pressure function q(0) = rho Ek - |m|^2 / 2 of U itself.
 struct Bnd {
-  float lo, hi, kk;
+  float gap_lo, gap_hi, Ek, C;
 };
 
 template <int TY>
@@ -147,46 +149,47 @@ __device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float
   return sub(gR, boost(gL, PR.y - PL.y, PR.z - PL.z));
 }
 
-// Largest theta in [0, 1] keeping U0 + theta D admissible and inside the
-// relaxed density bounds [lo_b, hi_b], in the cell's rest frame (no
-// cancellation in the pressure quadratic).  The floors eps_rho, eps_p are
-// min(value, max(eps_pos, 1e-5 value)) of the first-order state U0: the
-// relative margin keeps the final average admissible despite FP32 rounding.
-// theta = 1 is tested first, inline and without any division (theta_one, the
-// common case); the general case is a call.  The constants come by value so
-// that no context struct lives in local memory.
-__device__ __forceinline__ float theta_star_general(const float4 U0, const float4 D, float lower, float hi_b,
-                                                 float kk) {
-  // every branch of the rule is evaluated and the taken one selected, so
-  // the lanes of a warp that enter here stay converged
-  const float vx = U0.x + D.x;
-  const bool below = vx < lower, above = !below && vx > hi_b;
-  const float lim = __fdividef(below ? U0.x - lower : hi_b - U0.x, below ? -D.x : D.x);
-  float th = (below || above) ? lim : 1.0f;
-  th = fminf(fmaxf(th, 0.0f), 1.0f);
-  const float C = fmaf(U0.x, U0.w - kk, -0.5f * fmaf(U0.y, U0.y, U0.z * U0.z));
-  const float Bq = fmaf(U0.x, D.w, fmaf(D.x, U0.w - kk, -fmaf(U0.y, D.y, U0.z * D.z)));
-  const float A = fmaf(D.x, D.w, -0.5f * fmaf(D.y, D.y, D.z * D.z));
-  const bool ok_th = fmaf(th, fmaf(th, A, Bq), C) >= 0.0f;
-  // the linear root (A = 0)
-  const float r_lin = __fdividef(-C, Bq);
-  // the quadratic's roots, the smallest positive one
-  const float sq = sqrtf(fmaxf(fmaf(Bq, Bq, -4.0f * A * C), 0.0f));
-  const float Q = -0.5f * (Bq + copysignf(sq, Bq));
-  const float r1q = __fdividef(Q, A), r2q = __fdividef(C, Q);
-  float r = r1q > 0.0f ? r1q : -1.0f;
-  r = (r2q > 0.0f && (r < 0.0f || r2q < r)) ? r2q : r;
-  const bool zero_q = Q == 0.0f || r < 0.0f;
-  const float rr = A == 0.0f ? r_lin : r;
-  const float root = fminf(fmaxf(rr, 0.0f), th);
-  return ok_th ? th : ((C <= 0.0f || (A != 0.0f && zero_q)) ? 0.0f : root);
+// The R-theta limit of one side of a face: the largest theta in [0, 1]
+// keeping V(theta) = U + theta D admissible and inside the relaxed density
+// bounds, D = -+4 d_f seen in the side's own (rest) frame, so the pressure
+// quadratic has no cancellation.  The floors eps_rho, eps_p are
+// min(value, max(eps_pos, 1e-5 value)) of U: the relative margin keeps the
+// final average admissible despite FP32 rounding.
+//
+// side_bound: the density limit th_rho (linear in theta), the coefficients of
+// q(theta) = rho E - |m|^2 / 2 - eps_p rho / (gamma - 1) = A theta^2 + Bq theta
+// + C, and whether q(th_rho) < 0 (the pressure then binds first).  Branch free.
+__device__ __forceinline__ float side_bound(const float4 U, const Bnd b, const float4 D, float& A, float& Bq,
+                                            bool& binds) {
+  const float ax = fabsf(D.x);
+  const float gap = D.x < 0.0f ? b.gap_lo : b.gap_hi;
+  const float th = ax <= gap ? 1.0f : __fdividef(gap, ax);
+  A = fmaf(D.x, D.w, -0.5f * fmaf(D.y, D.y, D.z * D.z));
+  Bq = fmaf(U.x, D.w, fmaf(D.x, b.Ek, -fmaf(U.y, D.y, U.z * D.z)));
+  binds = !(fmaf(th, fmaf(th, A, Bq), b.C) >= 0.0f);
+  return th;
 }
 
-// theta = 1 admissible: V = U0 + D inside the density limits with
-// q(1) = rho E - |m|^2 / 2 - kk rho >= 0.
-__device__ __forceinline__ bool theta_one(const float4 U0, const float4 D, const Bnd b) {
-  const float4 V = add(U0, D);
-  return V.x >= b.lo && V.x <= b.hi && fmaf(V.x, V.w - b.kk, -0.5f * fmaf(V.y, V.y, V.z * V.z)) >= 0.0f;
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// The pressure root where it binds: C = q(0) > 0 > q(th) leaves exactly one
+// root in (0, th), the smallest positive one.  The stable form
+// Q = -(Bq + sign(Bq) sqrt(Bq^2 - 4 A C)) / 2 gives the roots Q / A and C / Q,
+// and the one sought is C / Q when Q > 0, else Q / A: for A > 0 both roots
+// are positive, Bq < 0, Q > 0 and C / Q is the smaller; for A < 0 the roots
+// have opposite signs, and C / Q is the positive one exactly when Q > 0; for
+// A = 0, Q = -Bq > 0 and C / Q = -C / Bq.  C <= 0 (U itself on the floor)
+// gives 0.  The square root is the hardware approximation (relative error of
+// a few ulp): the 1e-5 margin of the floors absorbs it.
+__device__ __forceinline__ float side_root(float th, float A, float Bq, float C) {
+  const float sq = sqrt_approx(fmaxf(fmaf(Bq, Bq, -4.0f * (A * C)), 0.0f));
+  const float Q = -0.5f * (Bq + copysignf(sq, Bq));
+  const float r = Q > 0.0f ? __fdividef(C, Q) : __fdividef(Q, A);
+  return C > 0.0f ? fminf(fmaxf(r, 0.0f), th) : 0.0f;
 }
 
 __device__ __forceinline__ bool is_boundary(int i, int j, int nx, int ny) {
@@ -272,9 +275,10 @@ __device__ __forceinline__ void node_p2(const float4 Pc, const float4 PW, const 
   const float er = fminf(U.x, fmaxf(k.eps, 1e-5f * U.x));
   const float pLF = k.gm1 * fmaf(-0.5f, __fdividef(fmaf(U.y, U.y, U.z * U.z), U.x), U.w);
   const float ep = fminf(pLF, fmaxf(k.eps, 1e-5f * pLF));
-  B.lo = fmaxf(er, lo - delta);
-  B.hi = hi + delta;
-  B.kk = ep * k.rg;
+  B.gap_lo = U.x - fmaxf(er, lo - delta);
+  B.gap_hi = (hi + delta) - U.x;
+  B.Ek = U.w - ep * k.rg;
+  B.C = fmaf(U.x, B.Ek, -0.5f * fmaf(U.y, U.y, U.z * U.z));
 }
 
 // The exact a_{n-1} -> a_n change of a rest-frame non-equilibrium part:
@@ -291,41 +295,42 @@ __device__ __forceinline__ float4 a_change_y(const float4 g, const float4 P, flo
 }
 
 // theta_f of face (L, R) and theta_f d_f in L's and R's frames; gL, gR are the
-// face's outgoing part of L and incoming part of R, already at a_n.
+// face's outgoing part of L and incoming part of R, already at a_n.  Both
+// sides' density limits and pressure tests are evaluated unconditionally
+// (no lane of a warp waits for another); a pressure root is taken, one side
+// per pass, only where the pressure binds.  A boundary node sets no limit.
 __device__ __forceinline__ float face_theta(const float4 PL, const float4 PR, const float4 gL, const float4 gR,
                                             const float4 UL, const Bnd BL, const float4 UR, const Bnd BR,
                                             bool bL, bool bR, int limiter, const Ctx& k, float4& tdL, float4& tdR) {
+  const float4 dL = d_in_L(gL, gR, PL, PR);
+  const float4 dR = d_in_R(gL, gR, PL, PR);
   float th;
-  float4 dL = f4(0.f, 0.f, 0.f, 0.f), dR = dL;
-  if ((bL && bR) || limiter == 0) {
+  if (limiter == 0) {
     th = 0.0f;
+  } else if (limiter == 1) {
+    th = 1.0f;
   } else {
-    dL = d_in_L(gL, gR, PL, PR);
-    dR = d_in_R(gL, gR, PL, PR);
-    if (limiter == 1) {
-      th = 1.0f;
-    } else {
-      const float4 DL = scale(-4.f, dL), DR = scale(4.f, dR);
-      float tL = 1.0f, tR = 1.0f;
-      // sides whose theta = 1 test fails take the general case; one side per
-      // pass, so a warp runs it as often as its lanes need it most, not once
-      // per side that any lane needs
-      int pend = ((!bL && !theta_one(UL, DL, BL)) ? 1 : 0) | ((!bR && !theta_one(UR, DR, BR)) ? 2 : 0);
-      while (pend) {
-        const bool sl = (pend & 1) != 0;
-        const Bnd b = sl ? BL : BR;
-        const float t = theta_star_general(sl ? UL : UR, sl ? DL : DR, b.lo, b.hi, b.kk);
-        if (sl) {
-          tL = t;
-          pend &= 2;
-        } else {
-          tR = t;
-          pend = 0;
-        }
+    float AL, BqL, AR, BqR;
+    bool nL, nR;
+    float tL = side_bound(UL, BL, scale(-4.f, dL), AL, BqL, nL);
+    float tR = side_bound(UR, BR, scale(4.f, dR), AR, BqR, nR);
+    tL = bL ? 1.0f : tL;
+    tR = bR ? 1.0f : tR;
+    int pend = (nL && !bL ? 1 : 0) | (nR && !bR ? 2 : 0);
+    while (pend) {
+      const bool sl = (pend & 1) != 0;
+      const float t = side_root(sl ? tL : tR, sl ? AL : AR, sl ? BqL : BqR, sl ? BL.C : BR.C);
+      if (sl) {
+        tL = t;
+        pend &= 2;
+      } else {
+        tR = t;
+        pend = 0;
       }
-      th = fminf(tL, tR);
     }
+    th = fminf(tL, tR);
   }
+  th = (bL && bR) ? 0.0f : th;
   tdL = scale(th, dL);
   tdR = scale(th, dR);
   return th;
@@ -724,9 +729,9 @@ __device__ __forceinline__ float4 shfl_down4(const float4 v) {
   return f4(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1),
             __shfl_down_sync(0xffffffffu, v.z, 1), __shfl_down_sync(0xffffffffu, v.w, 1));
 }
-__device__ __forceinline__ Bnd shfl_down3(const Bnd v) {
-  return Bnd{__shfl_down_sync(0xffffffffu, v.lo, 1), __shfl_down_sync(0xffffffffu, v.hi, 1),
-             __shfl_down_sync(0xffffffffu, v.kk, 1)};
+__device__ __forceinline__ Bnd shfl_down_b(const Bnd v) {
+  return Bnd{__shfl_down_sync(0xffffffffu, v.gap_lo, 1), __shfl_down_sync(0xffffffffu, v.gap_hi, 1),
+             __shfl_down_sync(0xffffffffu, v.Ek, 1), __shfl_down_sync(0xffffffffu, v.C, 1)};
 }
 
 // blockIdx.x = (strip, row chunk) over all levels, blockIdx.y = realization;
@@ -802,13 +807,13 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
   float4 M1, M2, M3, M4;
   float4 Pq = ldP(ra), Pq1 = ldP(ra + 1), Fq1 = ldF(ra + 1);
   float4 Uq = z4, PEq;
-  Bnd Bq{0.f, 0.f, 0.f};
+  Bnd Bq{0.f, 0.f, 0.f, 0.f};
   float thS;
   float4 tdRS, g4q;
   {
     const float4 Pm2 = ldP(ra - 2), Pm = ldP(ra - 1), Fm = ldF(ra - 1), Fq = ldF(ra);
     float4 Um = z4;
-    Bnd Bm{0.f, 0.f, 0.f};
+    Bnd Bm{0.f, 0.f, 0.f, 0.f};
     const float4 PWm = west(Pm, Fm), PEm = east(Pm, Fm);
     if (inner(ra - 1)) node_p2(Pm, PWm, PEm, Pm2, Pq, k, Um, Bm, M1, M2, M3, M4);
     const float4 PWq = west(Pq, Fq);
@@ -869,7 +874,7 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
     }
     // P2 of row q + 1
     float4 U1 = z4;
-    Bnd B1{0.f, 0.f, 0.f};
+    Bnd B1{0.f, 0.f, 0.f, 0.f};
     const float4 PW1 = west(Pq1, Fq1), PE1 = east(Pq1, Fq1);
     const bool bq = !colin, b1 = !inner(q + 1);
     if (!b1) {
@@ -890,7 +895,7 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
     const float thN = face_theta(Pq, Pq1, G3, g4n, Uq, Bq, U1, B1, bq, b1, limiter, k, tdLN, tdRN);
     // east face (R = lane + 1); the west face comes from lane - 1
     const float4 gR = shfl_down4(G2), UR = shfl_down4(Uq);
-    const Bnd BR = shfl_down3(Bq);
+    const Bnd BR = shfl_down_b(Bq);
     float4 tdLE, tdRE;
     const float thE = face_theta(Pq, PEq, G1, gR, Uq, Bq, UR, BR, bq, !colin_e, limiter, k, tdLE, tdRE);
     const float thW = __shfl_up_sync(0xffffffffu, thE, 1);

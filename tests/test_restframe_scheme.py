@@ -258,3 +258,50 @@ def test_fp32_floor_margin_departure_is_small():
     rho, p, v = _compare(2, 12, margin=1e-5)
     assert rho < 1e-5 and v < 1e-5 and p < 2e-4, (rho, p, v)
     assert max(rho, p, v) > 1e-9  # the floors do bind somewhere: the check is not vacuous
+
+
+# ---- the kernel's limiter evaluation -----------------------------------------
+
+def kernel_theta(U0, D, gap_lo, gap_hi, Ek, gamma=GAMMA):
+    """theta* as the mixed kernel evaluates it (in FP64 here): the density
+    limit from the room below / above the bounds, then, only where
+    q(th_rho) < 0, the single root Q > 0 ? C / Q : Q / A of
+    q = A t^2 + B t + C (C = q(0) > 0 > q(th_rho) leaves one root in (0, th_rho))."""
+    ax = abs(D[0])
+    gap = gap_lo if D[0] < 0 else gap_hi
+    th = 1.0 if ax <= gap else gap / ax
+    A = D[0] * D[3] - 0.5 * (D[1] * D[1] + D[2] * D[2])
+    B = U0[0] * D[3] + D[0] * Ek - (U0[1] * D[1] + U0[2] * D[2])
+    C = U0[0] * Ek - 0.5 * (U0[1] ** 2 + U0[2] ** 2)
+    if C + th * (B + th * A) >= 0.0:
+        return th
+    if C <= 0.0:
+        return 0.0
+    sq = np.sqrt(max(B * B - 4.0 * A * C, 0.0))
+    Q = -0.5 * (B + (sq if B >= 0.0 else -sq))
+    r = C / Q if Q > 0.0 else Q / A
+    return min(max(r, 0.0), th)
+
+
+@pytest.mark.parametrize("frame", ["rest", "lab"])
+def test_kernel_limiter_rule_equals_oracle_limiter(frame):
+    # random first-order states and corrections, with the pressure binding in a
+    # good share of the cases; the oracle's theta_star is the reference
+    rng = np.random.default_rng(11)
+    binding = 0
+    for trial in range(2000):
+        rho0 = rng.uniform(0.1, 5)
+        v = rng.uniform(-800, 800, 2) if frame == "lab" else rng.uniform(-2, 2, 2)
+        p0 = 10 ** rng.uniform(-3, 1)
+        U0 = np.array([rho0, rho0 * v[0], rho0 * v[1], p0 * RG + 0.5 * rho0 * (v @ v)])
+        scale = np.array([rho0, rho0 * (abs(v).max() + 1), rho0 * (abs(v).max() + 1), U0[3]])
+        D = rng.standard_normal(4) * scale * 10 ** rng.uniform(-4, 0.5)
+        lo_b, hi_b = rho0 * rng.uniform(0.3, 1.0), rho0 * rng.uniform(1.0, 3.0)
+        eps_r, eps_p = min(1e-13, rho0), min(1e-13, p0)
+        ref = O.theta_star(U0, D, lo_b, hi_b, eps_r, eps_p, GAMMA)
+        got = kernel_theta(U0, D, rho0 - max(eps_r, lo_b), hi_b - rho0, U0[3] - eps_p * RG)
+        tol = 1e-12 if frame == "rest" else 1e-6  # lab-frame q cancels at |v| = 800
+        assert abs(got - ref) <= tol * max(ref, 1e-3), (trial, got, ref)
+        V = U0 + min(1.0, (rho0 - max(eps_r, lo_b)) / abs(D[0]) if D[0] < 0 else (hi_b - rho0) / D[0]) * D
+        binding += (V[0] * V[3] - 0.5 * (V[1] ** 2 + V[2] ** 2) - eps_p * RG * V[0]) < 0.0
+    assert binding > 200
