@@ -256,7 +256,8 @@ int stats_error_functionals(const void* ens_a, int a_is_f32, int nxa, int nya, c
  * and never calls cudaMalloc, cudaFree or any allocating routine; the caller
  * still passes the ensembles and the output array.  M must be <= 4096
  * (VLBM_EINVAL beyond).  The first call on a device looks up the array's
- * device address (make it before any stream capture on that device).  All
+ * device address: make it before any stream capture on that device (a first
+ * call on a capturing stream returns VLBM_ESTATE and enqueues nothing).  All
  * calls share the array: calls that overlap on the GPU race; consecutive
  * calls do not interfere (each overwrites every partial sum it reads).
  * Results are identical to stats_error_functionals.  The paper has no

@@ -713,8 +713,15 @@ int stats_error_functionals_noalloc(const void* ens_a, int a_is_f32, int nxa, in
                     " realizations the allocation-free scratch holds; use stats_error_functionals");
   int st = functional_check(nxa, nya, nxb, nyb, M, &why);
   if (st) return fail(nullptr, st, why);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cs);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaStreamIsCapturing");
   double* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(&scratch);
+  e = noalloc_scratch(&scratch, cs == cudaStreamCaptureStatusNone);
+  if (e == cudaErrorStreamCaptureUnsupported)
+    return fail(nullptr, VLBM_ESTATE,
+                "the first stats_error_functionals_noalloc call on a device must come before any stream capture "
+                "(it looks up the scratch array's device address)");
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the functional scratch");
   e = functional_launch(ens_a, a_is_f32, nxa, nya, ens_b, b_is_f32, nxb, M, scratch, out,
                         static_cast<cudaStream_t>(cuda_stream));

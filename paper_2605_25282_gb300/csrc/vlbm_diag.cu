@@ -239,8 +239,10 @@ int noalloc_max_m() { return kNoAllocMaxM; }
 
 // Device address of the scratch array for the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
-cudaError_t noalloc_scratch(double** out) {
+// once per device (with that device current) and cached.  With lookup false
+// an address not cached yet is not looked up (cudaErrorStreamCaptureUnsupported):
+// the lookup may load the module, which a stream capture does not allow.
+cudaError_t noalloc_scratch(double** out, bool lookup) {
   static std::mutex mu;
   static double* cached[64] = {};
   int dev = 0;
@@ -249,6 +251,7 @@ cudaError_t noalloc_scratch(double** out) {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(mu);
   if (!cached[dev]) {
+    if (!lookup) return cudaErrorStreamCaptureUnsupported;
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_functional_scratch);
     if (e != cudaSuccess) return e;
@@ -272,13 +275,12 @@ int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why
 
 cudaError_t functional_launch(const void* a, int a_f32, int nxa, int nya, const void* b, int b_f32, int nxb, int M,
                               double* scratch, double* out, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(functional_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         2 * 4096 * (int)sizeof(double));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(functional_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                2 * 4096 * (int)sizeof(double));
+  });
+  if (e != cudaSuccess) return e;
   const int r = nxb / nxa, P = pow2_at_least(M);
   double* partial = scratch;
   double* partial2 = scratch + 3 * kFuncCtas;
@@ -308,13 +310,12 @@ int quantile_launch(const void* ens, int f32, int nx, int ny, int M, const doubl
     k = k < 1 ? 1 : (k > M ? M : k);
     q.k[i] = k - 1;
   }
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(quantile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 8) != cudaSuccess) {
-      *why = "cudaFuncSetAttribute failed";
-      return VLBM_ECUDA;
-    }
-    configured = true;
+  static std::atomic<unsigned long long> configured{0};
+  if (once_per_device(configured, [] {
+        return cudaFuncSetAttribute(quantile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 8);
+      }) != cudaSuccess) {
+    *why = "cudaFuncSetAttribute failed";
+    return VLBM_ECUDA;
   }
   const int P = pow2_at_least(M);
   const size_t cells = (size_t)nx * ny;

@@ -14,6 +14,7 @@
 // count, so realizations that stop early (landing) keep a consistent state.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -111,6 +112,23 @@ __host__ __device__ inline double bits_to_lam(unsigned long long b) {
 // Counts kernel launches enqueued by the library (see vlbm_kernel_launches).
 void add_launches(unsigned n);
 
+// Runs set() once per device (the current one) for the flag word `done`.
+// Kernel attributes such as the dynamic shared-memory limit are per device,
+// so a process that uses several GPUs configures each of them.  Two threads
+// may both run set() for a device the first time; it is idempotent.
+template <class F>
+cudaError_t once_per_device(std::atomic<unsigned long long>& done, F set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return set();
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
 // Launch helpers implemented in the kernel translation units.
 cudaError_t launch_step_f64(const Launch& L, cudaStream_t s);
 size_t step_f64_smem_bytes();
@@ -134,7 +152,7 @@ cudaError_t restrict_launch(const void* ens, int is_f32, int nx, int ny, int M, 
 // report a status code and, on failure, a reason in *why.
 size_t functional_scratch_doubles(int M);
 int noalloc_max_m();
-cudaError_t noalloc_scratch(double** out);
+cudaError_t noalloc_scratch(double** out, bool lookup);
 int functional_check(int nxa, int nya, int nxb, int nyb, int M, const char** why);
 cudaError_t functional_launch(const void* a, int a_f32, int nxa, int nya, const void* b, int b_f32, int nxb, int M,
                               double* scratch, double* out, cudaStream_t s);

@@ -136,14 +136,12 @@ int stats_launch(const void* ens_a, int a_is_f32, int nxa, int nya, const void* 
   int P = 1;
   while (P < M) P <<= 1;
   const size_t smem = 2 * (size_t)P * sizeof(double);
-  static bool configured = false;
-  if (!configured) {
-    if (cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8) !=
-        cudaSuccess) {
-      *why = "cudaFuncSetAttribute failed for the statistics kernel";
-      return VLBM_ECUDA;
-    }
-    configured = true;
+  static std::atomic<unsigned long long> configured{0};
+  if (once_per_device(configured, [] {
+        return cudaFuncSetAttribute(stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
+      }) != cudaSuccess) {
+    *why = "cudaFuncSetAttribute failed for the statistics kernel";
+    return VLBM_ECUDA;
   }
   stats_kernel<<<nxa * nya, kStatThreads, smem, s>>>(ens_a, a_is_f32, nxa, nya, ens_b, b_is_f32, nxb, r, M, P,
                                                      mean_a, std_a, mean_b, std_b, w1);

@@ -356,13 +356,11 @@ __global__ void __launch_bounds__(NT, 1) step_f64_kernel(const Launch L) {
 size_t step_f64_smem_bytes() { return sizeof(Smem); }
 
 cudaError_t launch_step_f64(const Launch& L, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(Smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(step_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  });
+  if (e != cudaSuccess) return e;
   dim3 grid(L.total_tiles, L.M);
   step_f64_kernel<<<grid, NT, sizeof(Smem), s>>>(L);
   add_launches(1);

@@ -117,14 +117,6 @@ __device__ __forceinline__ float4 axpy(float s, float4 x, float4 y) {
   return cat4(__ffma2_rn(ss, lo2(x), lo2(y)), __ffma2_rn(ss, hi2(x), hi2(y)));
 }
 
-// B_w u of a node with primitive state P; d = velocity relative to w.
-__device__ __forceinline__ float4 boosted(const float4 P, float w1, float w2, const Ctx& k, float& d1, float& d2) {
-  d1 = P.y - w1;
-  d2 = P.z - w2;
-  const float r = P.x;
-  return f4(r, r * d1, r * d2, fmaf(0.5f * r, fmaf(d1, d1, d2 * d2), P.w * k.rg));
-}
-
 // Boosted lab fluxes B_w f(u) = f(u') + w1 u' and B_w g(u) = g(u') + w2 u'.
 __device__ __forceinline__ float4 xflux(const float4 u, float d1, float d2, float p, float w1) {
   return f4(fmaf(w1, u.x, u.y), fmaf(w1, u.y, fmaf(u.y, d1, p)), fmaf(w1, u.z, u.y * d2), fmaf(w1, u.w, (u.w + p) * d1));
@@ -248,6 +240,27 @@ __device__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t phase) {
 // bit-identical results (the translation unit is compiled without FMA
 // contraction; every fused multiply-add is an explicit fmaf).
 
+// Maxwellian of a neighbour node X (primitive state P) boosted into the frame
+// moving with w (Eqs. (maxwellians12), (maxwellians34) and the boost
+// identities): B_w M(u_X) = s u' + hs f(u') (x) or s u' + hs g(u') (y), with
+// u' = B_w u_X = (rho, rho d1, rho d2, E'), d = v_X - w the relative velocity,
+// E' = rho |d|^2 / 2 + p / (gamma - 1), s = c1 + hs w_dir and hs = +1/(2a)
+// for M_1, M_3, -1/(2a) for M_2, M_4.  With sig = s + hs d_dir (>= 0 under
+// the kinetic-speed bound) it reads
+//   x: (rho sig, rho sig d1 + hs p, rho sig d2, E' sig + hs p d1)
+//   y: (rho sig, rho sig d1, rho sig d2 + hs p, E' sig + hs p d2).
+template <int DIR>
+__device__ __forceinline__ float4 maxwellian_in_frame(const float4 P, float w1, float w2, float s, float hs,
+                                                      float rg) {
+  const float d1 = P.y - w1, d2 = P.z - w2;
+  const float sig = fmaf(hs, DIR == 1 ? d1 : d2, s);
+  const float rs = P.x * sig;
+  const float hp = hs * P.w;
+  const float Ep = fmaf(0.5f * P.x, fmaf(d1, d1, d2 * d2), P.w * rg);
+  if (DIR == 1) return f4(rs, fmaf(rs, d1, hp), rs * d2, fmaf(Ep, sig, hp * d1));
+  return f4(rs, rs * d1, fmaf(rs, d2, hp), fmaf(Ep, sig, hp * d2));
+}
+
 // P2 of an interior node c: U_LF (Eq. (vlbm5)'s first-order part) and the
 // relaxed density bounds, in c's own frame, and the four boosted upwind
 // Maxwellians B_vc M_k(u_upwind) (Eqs. (maxwellians12), (maxwellians34)).
@@ -255,15 +268,10 @@ __device__ __forceinline__ void node_p2(const float4 Pc, const float4 PW, const 
                                         const float4 PN, const Ctx& k, float4& U, Bnd& B, float4& M1, float4& M2,
                                         float4& M3, float4& M4) {
   const float w1 = Pc.y, w2 = Pc.z;
-  float d1, d2;
-  const float4 uW = boosted(PW, w1, w2, k, d1, d2);
-  M1 = axpy(k.h, xflux(uW, d1, d2, PW.w, w1), scale(k.c1, uW));
-  const float4 uE = boosted(PE, w1, w2, k, d1, d2);
-  M2 = axpy(-k.h, xflux(uE, d1, d2, PE.w, w1), scale(k.c1, uE));
-  const float4 uS = boosted(PS, w1, w2, k, d1, d2);
-  M3 = axpy(k.h, yflux(uS, d1, d2, PS.w, w2), scale(k.c1, uS));
-  const float4 uN = boosted(PN, w1, w2, k, d1, d2);
-  M4 = axpy(-k.h, yflux(uN, d1, d2, PN.w, w2), scale(k.c1, uN));
+  M1 = maxwellian_in_frame<1>(PW, w1, w2, fmaf(k.h, w1, k.c1), k.h, k.rg);
+  M2 = maxwellian_in_frame<1>(PE, w1, w2, fmaf(-k.h, w1, k.c1), -k.h, k.rg);
+  M3 = maxwellian_in_frame<2>(PS, w1, w2, fmaf(k.h, w2, k.c1), k.h, k.rg);
+  M4 = maxwellian_in_frame<2>(PN, w1, w2, fmaf(-k.h, w2, k.c1), -k.h, k.rg);
   U = add(add(M1, M2), add(M3, M4));
   if (k.alpha != 0.0f) U = add(U, f4(k.alpha * Pc.x, 0.0f, 0.0f, (k.alpha * Pc.w) * k.rg));
   const float lo = fminf(fminf(Pc.x, fminf(PW.x, PE.x)), fminf(fminf(PS.x, PN.x), U.x));
@@ -996,14 +1004,12 @@ cudaError_t layout(Launch& L) {
 
 template <int TY>
 cudaError_t launch_tile(Launch& L, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_mixed_tile_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(SmemTile<TY>));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  cudaError_t e = layout<TY>(L);
+  static std::atomic<unsigned long long> configured{0};
+  cudaError_t e = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(step_mixed_tile_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(SmemTile<TY>));
+  });
+  if (e == cudaSuccess) e = layout<TY>(L);
   if (e != cudaSuccess) return e;
   step_mixed_tile_kernel<TY><<<dim3(L.total_tiles, L.M), TX * TY, sizeof(SmemTile<TY>), s>>>(L);
   add_launches(1);
@@ -1012,20 +1018,21 @@ cudaError_t launch_tile(Launch& L, cudaStream_t s) {
 
 template <int TY>
 cudaError_t launch_persistent(Launch& L, cudaStream_t s) {
-  static int grid_ctas = 0;
-  if (!grid_ctas) {
-    const int smem = (int)sizeof(SmemPersist<TY>);
-    cudaError_t e = cudaFuncSetAttribute(step_mixed_persistent_kernel<TY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int per_sm = 0, dev = 0, sms = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mixed_persistent_kernel<TY>, TX * TY, smem);
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    grid_ctas = (per_sm > 0 ? per_sm : 1) * sms;
-  }
-  cudaError_t e = layout<TY>(L);
+  // one persistent CTA per SM slot: the occupancy and the SM count are those
+  // of the current device
+  static std::atomic<unsigned long long> configured{0};
+  const int smem = (int)sizeof(SmemPersist<TY>);
+  cudaError_t e = once_per_device(configured, [smem] {
+    return cudaFuncSetAttribute(step_mixed_persistent_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mixed_persistent_kernel<TY>, TX * TY, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid_ctas = (per_sm > 0 ? per_sm : 1) * sms;
+  e = layout<TY>(L);
   if (e != cudaSuccess) return e;
   const long long units = (long long)L.M * L.total_tiles;
   const int grid = (int)(units < grid_ctas ? units : grid_ctas);

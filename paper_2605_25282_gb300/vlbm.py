@@ -463,16 +463,22 @@ def stats_error_functionals_noalloc(ens_a: torch.Tensor, ens_b: torch.Tensor, ou
     device allocation by the library (scratch in a fixed device array, M <= 4096)."""
     _require_cuda()
     lib = load_library()
+    if not (ens_a.is_cuda and ens_b.is_cuda and out.is_cuda):
+        raise ValueError("ensembles and out must be CUDA tensors")
+    if not (ens_a.device == ens_b.device == out.device):
+        raise ValueError("ensembles and out must be on one device")
     if not (ens_a.is_contiguous() and ens_b.is_contiguous() and out.is_contiguous()):
         raise ValueError("ensembles and out must be contiguous device tensors")
     if out.dtype != torch.float64 or out.numel() < 4:
         raise ValueError("out must be a float64 device tensor with 4 elements")
     M, nya, nxa = ens_a.shape
     _, nyb, nxb = ens_b.shape
-    s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
-    _check(lib.stats_error_functionals_noalloc(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya,
-                                               _ptr(ens_b), int(ens_b.dtype == torch.float32), nxb, nyb, M,
-                                               _ptr(out), ctypes.c_void_p(s.cuda_stream)))
+    # the scratch array is resolved for the current device: make it the tensors' one
+    with torch.cuda.device(ens_a.device):
+        s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
+        _check(lib.stats_error_functionals_noalloc(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya,
+                                                   _ptr(ens_b), int(ens_b.dtype == torch.float32), nxb, nyb, M,
+                                                   _ptr(out), ctypes.c_void_p(s.cuda_stream)))
     return out
 
 

@@ -1,0 +1,74 @@
+"""Parity on the paper's own geometry (Sec. 2.2 and Sec. 3.3): the jet on
+[0, 2.5] x [-1, 1] with square cells, the 5:4 grids of the paper's ladder
+(the coarsest, 500 x 400, and half of it, 250 x 200), passed through
+vlbm_grid with y_min = -1 and y_max = 1.  (125 x 100 is not used: its row
+centres include |y| = 0.05 = r_jet exactly, a tie that rounding decides.)
+
+- FP64 path: every cell of every field after 10 steps within 1e-12 of the
+  oracle (norms of tests/gpu_helpers.py), both grids in one launch.
+- Mixed path: rho and v within 1e-4, p within 2e-3 (the bounds of
+  tests/test_gpu_mixed.py and their reasons) after 10 steps.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_25282_gb300 import vlbm
+from tests import gpu_helpers as H
+
+LEVELS = [(250, 200), (500, 400)]
+M, N = 2, 10
+
+
+def paper_grid(nx, ny):
+    return vlbm.Grid(nx, ny, 2.5, -1.0, 1.0)
+
+
+def oracle_paper(nx, ny):
+    return O.run_jet(O.Grid(nx, ny, x_max=2.5, y_min=-1.0), H.oracle_params(), O.Jet(), 0, 0, M, N)
+
+
+@pytest.mark.parametrize("nx,ny", LEVELS + [(1000, 800), (2000, 1600), (4000, 3200)])
+def test_paper_grids_are_square_and_centred(nx, ny):
+    g = O.Grid(nx, ny, x_max=2.5, y_min=-1.0)
+    assert g.dx == pytest.approx(2.0 / ny, rel=1e-15)
+    # the jet rows |y_j| <= 0.05 are symmetric about y = 0, 0.1 / dx of them
+    y = g.y0 + (np.arange(ny) + 0.5) * g.dx
+    jet = np.abs(y) <= 0.05
+    assert jet.sum() == round(0.1 / g.dx) and np.array_equal(jet, jet[::-1])
+
+
+@pytest.mark.gpu
+def test_fp64_paper_domain_10_steps():
+    ens = vlbm.Ensemble([paper_grid(*lv) for lv in LEVELS], precision="fp64", relax=H.relax())
+    ens.init(0, M)
+    ens.step(N)
+    for l, (nx, ny) in enumerate(LEVELS):
+        ref = oracle_paper(nx, ny)
+        u, pops = map(H.to_np, ens.get_state(l))
+        assert H.rel_err_cons(u, ref["u"]).max() <= 1e-12, l
+        assert H.rel_err_pressure(u, ref["u"]).max() <= 1e-12, l
+        assert H.rel_err_pops(pops, ref["pops"], ref["u"]).max() <= 1e-12, l
+        t, s = ens.time(l)
+        assert np.all(s == N) and np.allclose(t, ref["t"], rtol=1e-14, atol=0)
+        # the jet entered the domain on its axis
+        assert np.abs(u[:, 1, ny // 2, 1:4]).max() > 100.0
+
+
+@pytest.mark.gpu
+def test_mixed_paper_domain_10_steps():
+    ens = vlbm.Ensemble([paper_grid(*lv) for lv in LEVELS], precision="mixed", relax=H.relax())
+    ens.init(0, M)
+    ens.step(N)
+    for l, (nx, ny) in enumerate(LEVELS):
+        ref = oracle_paper(nx, ny)
+        g = O.Grid(nx, ny, x_max=2.5, y_min=-1.0)
+        mo = {k: H.to_np(v) for k, v in ens.moments(l).items()}
+        for m in range(M):
+            rho, v1, v2, p = O.moments(g, H.oracle_params(), ref["u"][m])
+            c = np.sqrt(5.0 / 3.0 * p / rho)
+            vs = np.abs(v1) + np.abs(v2) + c
+            assert (np.abs(mo["rho"][m] - rho) / rho).max() <= 1e-4, (l, m)
+            assert (np.maximum(np.abs(mo["u"][m] - v1), np.abs(mo["v"][m] - v2)) / vs).max() <= 1e-4, (l, m)
+            assert (np.abs(mo["p"][m] - p) / p).max() <= 2e-3, (l, m)

@@ -11,6 +11,7 @@ import torch
 
 from oracle import oracle as O
 from tests import gpu_helpers as H
+from paper_2605_25282_gb300 import vlbm
 from tests import inputs
 
 pytestmark = pytest.mark.gpu
@@ -164,3 +165,29 @@ def test_fp64_positivity_over_smallest_config():
     assert np.all(s == 500)
     mo = ens.moments(0)
     assert float(mo["rho"].min()) > 0 and float(mo["p"].min()) > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_realization_block_init_equals_slice_of_full_ensemble(precision):
+    # Sec. 3.1: realization m depends on (seed, m) only, so a block of
+    # realizations m_begin .. m_begin + M - 1 initialised on its own (what each
+    # rank of a multi-GPU run does) advances exactly like the same realizations
+    # of the whole ensemble; two levels at once
+    levels = [(64, 32), (128, 64)]
+    blk = vlbm.Ensemble(levels, precision=precision, relax=H.relax())
+    blk.init(0, 2, m_begin=3)
+    full = H.gpu_jet(levels, 5, precision=precision)
+    blk.step(12)
+    full.step(12)
+    for l in range(len(levels)):
+        ub, _ = blk.get_state(l)
+        uf, _ = full.get_state(l, 3, 2)
+        assert torch.equal(ub, uf), l
+        tb, sb = blk.time(l)
+        tf, sf = full.time(l)
+        assert np.array_equal(tb, tf[3:5]) and np.array_equal(sb, sf[3:5])
+    if precision == "fp64":
+        # and it is the oracle's realizations 3 and 4
+        ref = H.oracle_jet(64, 32, 2, 12, m0=3)
+        u = H.to_np(blk.get_state(0)[0])
+        assert H.rel_err_cons(u, ref["u"]).max() <= RTOL64
