@@ -39,9 +39,10 @@ BYTES_PER_UPDATE = {"mixed": 160, "fp64": 320}
 # DRAM traffic of one step-kernel launch from an ncu capture, with the sha256
 # of the kernel source and the launch design it was taken on (reported as null
 # once either differs).  Mixed: 606.8 MB read + written for the 4.0 M
-# cell-updates of the M = 10 capture, scaled to 400 M cell-updates.
+# cell-updates of the M = 10 capture (333.4 MB read + 273.4 MB written),
+# scaled to 400 M cell-updates.
 NCU_TRAFFIC = {
-    "mixed": {"sha": "2afd2e9bafeaf439", "design": "march30pf4w", "bytes_per_launch": 60.68e9,
+    "mixed": {"sha": "7dfbe44174883ad5", "design": "march30pf4w", "bytes_per_launch": 60.68e9,
               "capture": "M=10, 400x200 + 800x400, scaled by cell-updates"},
 }
 # The FP64 step kernel is bound by the FP64 pipe, not by HBM.  ncu counters of
@@ -247,6 +248,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _stat_errors(vlbm, a, b, stream):
+    """L1-normalised errors of the per-cell mean and std of ensemble a against
+    ensemble b, and their one-point W1 over sum |mean_b| (Sec. 3.2)."""
+    st = vlbm.stats_w1_mean_std(a, b, stream=stream)
+    ma, sa, mb, sb, w1 = (st[k].double() for k in ("mean_a", "std_a", "mean_b", "std_b", "w1"))
+    return {"mean": float((ma - mb).abs().sum() / mb.abs().sum()),
+            "std": float((sa - sb).abs().sum() / sb.abs().sum()),
+            "w1": float(w1.sum() / mb.abs().sum())}
+
+
+def precision_legs(vlbm, levels, args, stream, m_begin):
+    """Seed-matched ensembles of M = stat_m realizations: the mixed path, the
+    FP64 path on 2M realizations (the second half an independent ensemble of
+    the same size: the Monte-Carlo error at matched M) and an FP64 control
+    whose KL amplitudes differ by 1e-7 relative (the jet's own pathwise
+    divergence from a perturbation of FP32 size).  Statistic errors after 64
+    steps and at the final time; the FP64 and mixed rates over the same run."""
+    import torch
+
+    M = args.stat_m
+    horizon = args.t_final if args.t_final > 0 else None
+    amp = [0.1 * k ** -2.0 * (1.0 + 1e-7) for k in range(1, 11)]
+    runs = {"mixed": ("mixed", M, vlbm.PerturbParams()), "fp64": ("fp64", 2 * M, vlbm.PerturbParams()),
+            "control": ("fp64", M, vlbm.PerturbParams(amp=amp))}
+    dens, rates = {}, {}
+    for name, (p, m, pert) in runs.items():
+        for phase, n in (("short", 64), ("final", None)):
+            e = vlbm.Ensemble(levels, precision=p, stream=stream)
+            e.init(SEED, m, pert, m_begin=m_begin)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if n is not None:
+                e.step(n)
+            elif horizon is not None:
+                e.advance_to(horizon)
+            else:
+                e.step(args.solver_steps)
+            b.record(stream)
+            b.synchronize()
+            if phase == "final":
+                cells = sum(nx * ny * int(e.time(l)[1].sum()) for l, (nx, ny) in enumerate(levels))
+                rates[name] = {"value": cells / (a.elapsed_time(b) / 1e3) / 1e9, "M": m,
+                               "cell_updates": cells, "seconds": a.elapsed_time(b) / 1e3}
+            dens[(name, phase)] = [e.density(l, f32=False) for l in range(len(levels))]
+            e.close()
+    out = {"M": M, "norm": "sum over cells |s - s_ref| / sum |s_ref| (W1 between the ensembles: / sum |mean_ref|); "
+                           "the fine level restricted onto the coarse grid is not used: each level on its own",
+           "reference": "FP64 path (the oracle's arithmetic, equal to the oracle to 1e-12 per cell over 10 steps), "
+                        "same seed and realizations"}
+    for phase, label in (("short", "64 steps"), ("final", f"t = {horizon}" if horizon else "final")):
+        row = {"horizon": label}
+        for l, lname in enumerate(("coarse", "fine")):
+            ref = dens[("fp64", phase)][l][:M]
+            row[lname] = {
+                "mixed_vs_fp64": _stat_errors(vlbm, dens[("mixed", phase)][l], ref, stream),
+                "fp64_control_vs_fp64": _stat_errors(vlbm, dens[("control", phase)][l], ref, stream),
+                "independent_fp64_vs_fp64": _stat_errors(vlbm, dens[("fp64", phase)][l][M:], ref, stream)}
+        out[phase] = row
+    fp64 = {"value": rates["fp64"]["value"], "unit": "GLUPS", "M": rates["fp64"]["M"],
+            "horizon": "t = 0 to the final time (landing rule), the bench run's horizon",
+            "seconds": rates["fp64"]["seconds"], "mixed_same_run": rates["mixed"]}
+    return fp64, out
+
+
 def run_ours(args):
     import torch
 
@@ -375,49 +440,18 @@ def run_ours(args):
     ms_e2e, _, _, cells_all_e2e = timed_loop(True, 1)
     design = ens.step_design()
 
-    # the FP64 path on the same levels, fewer realizations (rate per cell update)
-    fp64 = None
-    if args.fp64_m > 0 and prec == "mixed":
-        e64 = vlbm.Ensemble(levels, precision="fp64", stream=stream)
-        e64.init(SEED, args.fp64_m, m_begin=m_begin)
-        e64.step(2)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e64.step(args.fp64_steps)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t64 = a.elapsed_time(b) / 1e3
-        c64 = sum(nx * ny for nx, ny in levels) * args.fp64_m * args.fp64_steps
-        r64 = c64 / t64 / 1e9
-        hbm, src = peaks()
-        fp64 = {"value": r64, "unit": "GLUPS", "M": args.fp64_m, "solver_steps": args.fp64_steps,
-                "hbm_frac": r64 * 1e9 * BYTES_PER_UPDATE["fp64"] / (hbm * 1e9), "alu": fp64_alu(r64)}
-        e64.close()
-
-    # error of every statistic of the mixed path against the FP64 path (whose
-    # update is the oracle's arithmetic), same seed and realizations
-    stat_err = None
+    # The FP64 path (the oracle's arithmetic) and the statistic errors, on the
+    # bench's own horizon: seed-matched ensembles of the same levels run from
+    # t = 0 to the final time with the landing rule, like one bench run.
+    fp64, stat_err = None, None
     if args.stat_m > 0 and prec == "mixed":
-        stat_err = {"M": args.stat_m, "solver_steps": S, "reference": "FP64 path, same realizations",
-                    "norm": "sum over cells |s_mixed - s_fp64| / sum |s_fp64| (W1: / sum |mean_fp64|)"}
-        ens_m = vlbm.Ensemble(levels, precision="mixed", stream=stream)
-        ens_d = vlbm.Ensemble(levels, precision="fp64", stream=stream)
-        for e in (ens_m, ens_d):
-            e.init(SEED, args.stat_m, m_begin=m_begin)
-            e.step(S)
-        for l, name in enumerate(("coarse", "fine")):
-            st = vlbm.stats_w1_mean_std(ens_m.density(l, f32=False), ens_d.density(l, f32=False), stream=stream)
-            ma, sa, mb, sb, w1 = (st[k].double() for k in ("mean_a", "std_a", "mean_b", "std_b", "w1"))
-            stat_err[name] = {"mean": float((ma - mb).abs().sum() / mb.abs().sum()),
-                              "std": float((sa - sb).abs().sum() / sb.abs().sum()),
-                              "w1": float(w1.sum() / mb.abs().sum())}
-        ens_m.close()
-        ens_d.close()
-
+        fp64, stat_err = precision_legs(vlbm, levels, args, stream, m_begin)
     value = cells_all / (ms / 1e3) / 1e9
     e2e_value = cells_all_e2e / (ms_e2e / 1e3) / 1e9
     hbm, src = peaks()
+    if fp64 is not None:
+        fp64["hbm_frac"] = fp64["value"] * 1e9 * BYTES_PER_UPDATE["fp64"] / (hbm * 1e9)
+        fp64["alu"] = fp64_alu(fp64["value"])
     # the step kernels of the timed bench steps: algorithmic bytes of their
     # cell-updates over the CUDA-event time of the advances (ticks, landing
     # and the polling of active realizations included)
@@ -479,17 +513,20 @@ def run_ours(args):
                        "cell_updates_timed": cells_timed},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": M * 2 * K * 8,
+            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": M * 2 * K * 8 / n_snap,
                     "d2h_bytes_per_step": 5 * nxa * nya * 8,
-                    "note": "host wall clock through the public API: every step copies the KL coefficients "
-                            "of all realizations from pinned host memory (vlbm_init_ensemble_samples), "
-                            "advances, and reads the statistics back to pinned host memory"},
+                    "note": f"host wall clock through the public API: the first step of every run (one in "
+                            f"{n_snap}) copies the KL coefficients of all realizations ({M * 2 * K * 8} B) from "
+                            "pinned host memory (vlbm_init_ensemble_samples); every step advances and reads "
+                            "the statistics back to pinned host memory; h2d_bytes_per_step is the average"},
             "gpu_launches": launches,
             "clocks": clk,
             "stats": stats,
             "fp64_path": fp64,
             "stat_error": stat_err,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+            "speedup_note": "the bench value over the FP64 path's rate, both over full runs from t = 0 to the "
+                            "final time of the same levels (FP64 at M = 2 x stat_m)",
         }
         print(json.dumps(line), flush=True)
     ens.close()
@@ -509,9 +546,8 @@ def main():
                     help="fixed steps per bench step when --t-final is 0; the statistic-error check's horizon")
     ap.add_argument("--t-final", type=float, default=0.0035, help="the run's final time (0: fixed steps)")
     ap.add_argument("--dt-snap", type=float, default=0.0005, help="output interval: one bench step per output time")
-    ap.add_argument("--fp64-m", type=int, default=50)
-    ap.add_argument("--fp64-steps", type=int, default=8)
-    ap.add_argument("--stat-m", type=int, default=16)
+    ap.add_argument("--stat-m", type=int, default=16,
+                    help="realizations of the precision legs (FP64 path rate, statistic errors); 0: skip them")
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -29,20 +29,29 @@ __device__ __forceinline__ void fluxes(const double q[4], double gamma, double f
 }
 
 // Largest theta in [0, 1] keeping U0 + theta D inside the admissible,
-// relaxed-bounded set (convex: the feasible thetas form [0, theta*]).
-static __device__ double theta_star(const double U0[4], const double D[4], double lo_b, double hi_b,
-                             double eps_r, double eps_p, double gamma) {
+// relaxed-bounded set (convex: the feasible thetas form [0, theta*]); the
+// pressure floor enters as kk = eps_p / (gamma - 1).
+static __device__ double theta_star_kk(const double U0[4], const double D[4], double lo_b, double hi_b,
+                                       double eps_r, double kk) {
+  // The density limits num / den lower theta only when num < den (a correctly
+  // rounded quotient of num >= den > 0 is >= 1), so the division runs only
+  // then: the same result as dividing always, for every input.
   double th = 1.0;
   const double lower = eps_r > lo_b ? eps_r : lo_b;
   if (D[0] < 0.0) {
-    const double lim = (U0[0] - lower) / (-D[0]);
-    if (lim < th) th = lim;
+    const double num = U0[0] - lower;
+    if (num < -D[0]) {
+      const double lim = num / (-D[0]);
+      if (lim < th) th = lim;
+    }
   } else if (D[0] > 0.0) {
-    const double lim = (hi_b - U0[0]) / D[0];
-    if (lim < th) th = lim;
+    const double num = hi_b - U0[0];
+    if (num < D[0]) {
+      const double lim = num / D[0];
+      if (lim < th) th = lim;
+    }
   }
   if (th < 0.0) th = 0.0;
-  const double kk = eps_p / (gamma - 1.0);
   const double C = U0[0] * U0[3] - 0.5 * (U0[1] * U0[1] + U0[2] * U0[2]) - kk * U0[0];
   const double B = U0[0] * D[3] + D[0] * U0[3] - (U0[1] * D[1] + U0[2] * D[2]) - kk * D[0];
   const double A = D[0] * D[3] - 0.5 * (D[1] * D[1] + D[2] * D[2]);
@@ -68,6 +77,11 @@ static __device__ double theta_star(const double U0[4], const double D[4], doubl
   if (r > th) r = th;
   if (r < 0.0) r = 0.0;
   return r;
+}
+
+static __device__ double theta_star(const double U0[4], const double D[4], double lo_b, double hi_b,
+                                    double eps_r, double eps_p, double gamma) {
+  return theta_star_kk(U0, D, lo_b, hi_b, eps_r, eps_p / (gamma - 1.0));
 }
 
 __device__ __forceinline__ bool is_boundary(int i, int j, int nx, int ny) {

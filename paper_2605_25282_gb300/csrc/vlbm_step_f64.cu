@@ -34,7 +34,7 @@ struct Smem {
   double f[4][HY][HX];
   double g[4][HY][HX];
   double ulf[4][GY][GX];
-  double bnd[4][GY][GX];  // lo_b, hi_b, eps_rho, eps_p
+  double bnd[4][GY][GX];  // lo_b, hi_b, eps_rho, eps_p / (gamma - 1)
   // per face: theta, the two non-equilibrium terms M_out(u_L) - u_out,L and
   // M_in(u_R) - u_in,R, and the two streamed populations of Eqs. (vlbm1)-(vlbm4)
   double thx[TY][TX + 1];
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NT, 1) step_f64_kernel(const Launch L) {
     S.bnd[0][lj][li] = lo - delta;
     S.bnd[1][lj][li] = hi + delta;
     S.bnd[2][lj][li] = L.ph.eps_pos < U[0] ? L.ph.eps_pos : U[0];
-    S.bnd[3][lj][li] = L.ph.eps_pos < pLF ? L.ph.eps_pos : pLF;
+    S.bnd[3][lj][li] = (L.ph.eps_pos < pLF ? L.ph.eps_pos : pLF) / (gamma - 1.0);
   }
   __syncthreads();
 
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(NT, 1) step_f64_kernel(const Launch L) {
           U0[c] = S.ulf[c][gy][gx];
           DD[c] = -4.0 * d[c];
         }
-        tL = theta_star(U0, DD, S.bnd[0][gy][gx], S.bnd[1][gy][gx], S.bnd[2][gy][gx], S.bnd[3][gy][gx], gamma);
+        tL = theta_star_kk(U0, DD, S.bnd[0][gy][gx], S.bnd[1][gy][gx], S.bnd[2][gy][gx], S.bnd[3][gy][gx]);
       }
       if (!bR) {
         const int gx = iR - i0 + 1, gy = jR - j0 + 1;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(NT, 1) step_f64_kernel(const Launch L) {
           U0[c] = S.ulf[c][gy][gx];
           DD[c] = 4.0 * d[c];
         }
-        tR = theta_star(U0, DD, S.bnd[0][gy][gx], S.bnd[1][gy][gx], S.bnd[2][gy][gx], S.bnd[3][gy][gx], gamma);
+        tR = theta_star_kk(U0, DD, S.bnd[0][gy][gx], S.bnd[1][gy][gx], S.bnd[2][gy][gx], S.bnd[3][gy][gx]);
       }
       th = tL < tR ? tL : tR;
     }

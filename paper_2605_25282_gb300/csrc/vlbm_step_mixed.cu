@@ -1042,14 +1042,30 @@ cudaError_t launch_persistent(Launch& L, cudaStream_t s) {
 }
 
 // Strips of kMW columns; rows split into chunks of kMNW warps with about
-// kMarchRows rows per warp.
+// kMarchRows rows per warp, fewer (down to 4) when the launch would not give
+// every SM two rounds of MINB CTAs (a single small grid): each warp then
+// re-evaluates one more halo row per fewer rows, but the GPU fills.  The
+// split does not change any result.
 template <int MINB, bool PF>
 cudaError_t launch_march(Launch& L, cudaStream_t s) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int target = kMarchRows;
+  for (;;) {
+    long long ctas = 0;
+    for (int l = 0; l < L.nlevels; ++l) {
+      const LevelDesc& D = L.lv[l];
+      const int rows = D.ny - 2;
+      ctas += (long long)((D.nx - 2 + kMW - 1) / kMW) * ((rows + kMNW * target - 1) / (kMNW * target));
+    }
+    if (ctas * L.M >= 2LL * sms * MINB || target <= 4) break;
+    target = target / 2 < 4 ? 4 : target / 2;
+  }
   int units = 0;
   for (int l = 0; l < L.nlevels; ++l) {
     LevelDesc& D = L.lv[l];
     const int rows = D.ny - 2;
-    const int chunks = (rows + kMNW * kMarchRows - 1) / (kMNW * kMarchRows);
+    const int chunks = (rows + kMNW * target - 1) / (kMNW * target);
     D.tiles_x = (D.nx - 2 + kMW - 1) / kMW;
     D.tiles_y = chunks;
     D.wrows = (rows + chunks * kMNW - 1) / (chunks * kMNW);

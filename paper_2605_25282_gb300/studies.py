@@ -301,12 +301,17 @@ def main(argv=None):
     ap.add_argument("--t", type=float, default=0.0035, help="final time (precision study)")
     ap.add_argument("--times", type=str, default="0.0005,0.001,0.002,0.0035", help="snapshot times (cauchy)")
     ap.add_argument("--peak-gbs", type=float, default=None)
+    ap.add_argument("--levels", type=str, default=None,
+                    help="ladder: levels as NXxNY,... (default: the refinement ladder 400x200 ... 5060x2530)")
+    ap.add_argument("--warmup", type=int, default=4, help="ladder: untimed steps before the timed ones")
     ap.add_argument("--control", action="store_true", help="precision: add a perturbed FP64 control run")
     ap.add_argument("--save", type=str, default=None, help="final: write the final state to this file")
     ap.add_argument("--load", type=str, default=None, help="resume: the state file written by final --save")
     args = ap.parse_args(argv)
     if args.study == "ladder":
-        res = ladder(args.precision or "fp64", args.steps, M=args.M or 1, peak_gbs=args.peak_gbs)
+        levels = LADDER_C2 if not args.levels else [tuple(int(v) for v in lv.split("x")) for lv in args.levels.split(",")]
+        res = ladder(args.precision or "fp64", args.steps, warmup=args.warmup, levels=levels, M=args.M or 1,
+                     peak_gbs=args.peak_gbs)
     elif args.study == "precision":
         res = precision_study(args.nx, args.ny, args.M or 64, args.t, args.control)
     elif args.study == "cauchy":
