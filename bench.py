@@ -46,15 +46,18 @@ NCU_TRAFFIC = {
               "capture": "M=10, 400x200 + 800x400, scaled by cell-updates"},
 }
 # The FP64 step kernel is bound by the FP64 pipe, not by HBM.  ncu counters of
-# one launch (M = 2, 400x200 + 800x400, 800,000 cell-updates), with the sha256
-# of the kernel source and of its math header: FP64-pipe warp instructions x 32
-# per cell-update (every FP64 add, multiply, fused multiply-add, compare,
-# min/max and conversion; an upper bound where lanes idle), and the FLOPs of
-# its adds, multiplies and fused multiply-adds (161.5 M DADD + 207.8 M DMUL +
-# 129.5 M DFMA thread instructions).  GB300 issues 2 FP64 thread operations per
-# SM and clock.
-FP64_ALU = {"sha": "72c2b9ea2d4f61d6+d4e76c39de7e1da7", "pipe_inst_per_update": 18172822 * 32 / 800000,
-            "flop_per_update": (161525984 + 207834288 + 2 * 129468696) / 800000, "ops_per_sm_clock": 2,
+# one launch of the warp-march design (M = 2, 400x200 + 800x400, 800,000
+# cell-updates, the first steps of a run), with the sha256 of the kernel source
+# and of its math header: FP64-pipe warp instructions x 32 per cell-update
+# (every FP64 add, multiply, fused multiply-add, compare, min/max and
+# conversion; the FP64 pipe runs all 32 lanes of a warp instruction), and the
+# FLOPs of its adds, multiplies and fused multiply-adds (165.1 M DADD +
+# 159.2 M DMUL + 107.0 M DFMA thread instructions).  GB300 issues 2 FP64
+# thread operations per SM and clock.  Later in a run the limiter divides and
+# takes pressure roots more often, so over a full run the instructions per
+# cell-update are more and the fraction below is a lower bound.
+FP64_ALU = {"sha": "70c3d6fa0a3e8455+54acf87532a47ae3", "pipe_inst_per_update": 15982684 * 32 / 800000,
+            "flop_per_update": (165147216 + 159229266 + 2 * 107026840) / 800000, "ops_per_sm_clock": 2,
             "sms": 152}
 
 

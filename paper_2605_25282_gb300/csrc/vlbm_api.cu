@@ -951,7 +951,14 @@ unsigned long long vlbm_kernel_launches(void) { return g_launches.load(); }
 
 int vlbm_step_design(const vlbm_ctx* c, int* index, const char** name, int* count) {
   if (!c) return VLBM_EINVAL;
-  const int v = c->precision == VLBM_MIXED ? c->variant : -1;
+  if (c->precision == VLBM_FP64) {
+    const int v = f64_variant();
+    if (index) *index = v;
+    if (name) *name = f64_variant_name(v);
+    if (count) *count = 2;
+    return VLBM_OK;
+  }
+  const int v = c->variant;
   if (index) *index = v;
   if (name) *name = v >= 0 ? mixed_variant_name(v) : "none";
   if (count) *count = mixed_variants();

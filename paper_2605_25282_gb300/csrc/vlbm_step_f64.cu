@@ -16,6 +16,7 @@
 // FP64 is the slow path on GB300 (1/58 of the FP32 rate): this kernel is
 // bound by the FP64 pipe, not by HBM.
 #include <cfloat>
+#include <cstdlib>
 
 #include "vlbm_f64_math.cuh"
 #include "vlbm_internal.cuh"
@@ -351,11 +352,371 @@ __global__ void __launch_bounds__(NT, 1) step_f64_kernel(const Launch L) {
   }
 }
 
+// ---- warp-marching design ----------------------------------------------------
+// A warp owns 28 interior columns (lanes 2..29; lanes 0, 1 and 30, 31 hold the
+// halo columns) and marches up D.wrows rows.  Each lane evaluates its own
+// node once per row (the state, its fluxes and its four Maxwellians
+// M_k(u; a_n)), x-neighbours' values come by warp shuffle, and a sliding
+// window of rows stays in registers: the tile design evaluates a node's fluxes
+// 1.69 times and U_LF 1.33 times per cell (its halos), this one 1.14 times
+// each.  The FP64 pipe executes every lane of a warp instruction, so no lane
+// takes extra halo work: with two halo lanes on each side every U_LF and face
+// the updated cells need is in the warp.  Every expression is the tile
+// design's (and the oracle's), in the same order: the results are identical.
+constexpr int kFW = 28;     // columns updated per warp
+constexpr int kFNW = 4;     // warps per CTA
+constexpr int kFRows = 16;  // target rows per warp
+
+// The state u of a node and its Maxwellians, Eqs. (maxwellians12), (maxwellians34):
+// M1 = c1 u + f / 2a, M2 = c1 u - f / 2a, M3 = c1 u + g / 2a, M4 = c1 u - g / 2a.
+struct NodeF64 {
+  double u[4], M1[4], M2[4], M3[4], M4[4];
+};
+
+__device__ __forceinline__ void eval_node(const double* __restrict__ src, size_t plane, size_t off, double gamma,
+                                          double c1, double inv2a, NodeF64& n) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) n.u[c] = __ldg(src + c * plane + off);
+  double f[4], g[4];
+  fluxes(n.u, gamma, f, g);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    n.M1[c] = c1 * n.u[c] + f[c] * inv2a;
+    n.M2[c] = c1 * n.u[c] - f[c] * inv2a;
+    n.M3[c] = c1 * n.u[c] + g[c] * inv2a;
+    n.M4[c] = c1 * n.u[c] - g[c] * inv2a;
+  }
+}
+
+// U_LF of an interior node (Eq. (vlbm5)'s first-order part) and its limits:
+// relaxed density bounds, eps_rho, eps_p / (gamma - 1).
+__device__ __forceinline__ void node_lf(const double u[4], const double M1W[4], const double M2E[4],
+                                        const double M3S[4], const double M4N[4], double rW, double rE, double rS,
+                                        double rN, const Physics& ph, double alpha, double gamma, double U[4],
+                                        double bnd[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) U[c] = alpha * u[c] + M1W[c] + M2E[c] + M3S[c] + M4N[c];
+  double lo = u[0], hi = lo;
+  const double rs5[5] = {rW, rE, rS, rN, U[0]};
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    lo = rs5[r] < lo ? rs5[r] : lo;
+    hi = rs5[r] > hi ? rs5[r] : hi;
+  }
+  const double delta = ph.rlmp_rel * (hi - lo) + ph.rlmp_abs;
+  double v1, v2, pLF;
+  primitive(U, gamma, v1, v2, pLF);
+  bnd[0] = lo - delta;
+  bnd[1] = hi + delta;
+  bnd[2] = ph.eps_pos < U[0] ? ph.eps_pos : U[0];
+  bnd[3] = (ph.eps_pos < pLF ? ph.eps_pos : pLF) / (gamma - 1.0);
+}
+
+// Face (L, R): theta_f, the non-equilibrium terms eo = Mo - pL, ei = Mi - pR
+// and the streamed populations no, ni (Eqs. (vlbm1)-(vlbm4)).  Mo = M_out(u_L),
+// Mi = M_in(u_R); pLraw, pRraw the stored populations (a boundary node's
+// stand in by its equilibrium).
+__device__ __forceinline__ void face_f64(const double Mo[4], const double Mi[4], const double pLraw[4],
+                                         const double pRraw[4], bool bL, bool bR, const double UL[4],
+                                         const double BL[4], const double UR[4], const double BR[4], int limiter,
+                                         double& th, double eo[4], double ei[4], double no[4], double ni[4]) {
+  double pL[4], pR[4], d[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    pL[c] = bL ? Mo[c] : pLraw[c];
+    pR[c] = bR ? Mi[c] : pRraw[c];
+    d[c] = (Mo[c] - pL[c]) - (Mi[c] - pR[c]);
+  }
+  if (bL && bR) {
+    th = 0.0;
+  } else if (limiter == 0) {
+    th = 0.0;
+  } else if (limiter == 1) {
+    th = 1.0;
+  } else {
+    double tL = 1.0, tR = 1.0;
+    if (!bL) {
+      double DD[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) DD[c] = -4.0 * d[c];
+      tL = theta_star_kk(UL, DD, BL[0], BL[1], BL[2], BL[3]);
+    }
+    if (!bR) {
+      double DD[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) DD[c] = 4.0 * d[c];
+      tR = theta_star_kk(UR, DD, BR[0], BR[1], BR[2], BR[3]);
+    }
+    th = tL < tR ? tL : tR;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    eo[c] = Mo[c] - pL[c];
+    ei[c] = Mi[c] - pR[c];
+    no[c] = Mo[c] + th * (Mo[c] - pL[c]);
+    ni[c] = Mi[c] + th * (Mi[c] - pR[c]);
+  }
+}
+
+__device__ __forceinline__ double shup(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ double shdn(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// blockIdx.x = (strip, row chunk) over all levels, blockIdx.y = realization.
+__global__ void __launch_bounds__(kFNW * 32, 1) step_f64_march_kernel(const Launch L) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int unit = blockIdx.x, lvl = 0;
+  while (lvl + 1 < L.nlevels && unit >= L.lv[lvl + 1].tile_begin) ++lvl;
+  const LevelDesc& D = L.lv[lvl];
+  unit -= D.tile_begin;
+  const int m = blockIdx.y;
+  RealState* rs = D.rs + m;
+  if (!rs->active) return;
+  const int nx = D.nx, ny = D.ny, nxp = D.nx_pad;
+  const int ra = 1 + ((unit / D.tiles_x) * kFNW + wid) * D.wrows;
+  const int rb = min(ra + D.wrows - 1, ny - 2);
+  if (ra > rb) return;
+  // lane l holds column 28 strip + l - 1 (lanes 2..29: the strip's columns)
+  const int c = (unit % D.tiles_x) * kFW + lane - 1;
+  const int cl = c < 0 ? 0 : (c > nx - 1 ? nx - 1 : c);
+  const bool upd = lane >= 2 && lane <= kFW + 1 && c <= nx - 2;
+  const bool colin = c >= 1 && c <= nx - 2;
+  const size_t plane = D.plane;
+  const int par = (int)(rs->steps & 1);
+  const double* __restrict__ src =
+      reinterpret_cast<const double*>(D.lat) + ((size_t)par * L.M + m) * D.real_stride;
+  double* __restrict__ dst = reinterpret_cast<double*>(D.lat) + ((size_t)(par ^ 1) * L.M + m) * D.real_stride;
+  const double inv2a = rs->inv2a;
+  const double gamma = L.ph.gamma, alpha = L.ph.alpha;
+  const double c1 = (1.0 - alpha) / 4.0;
+  const int limiter = L.ph.limiter;
+  auto off_of = [&](int row) {
+    const int r = row < 0 ? 0 : (row > ny - 1 ? ny - 1 : row);
+    return (size_t)r * nxp + cl;
+  };
+  auto pop = [&](int k, int row, double p[4]) {
+    const size_t o = off_of(row);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) p[cc] = __ldg(src + (size_t)(4 + k * 4 + cc) * plane + o);
+  };
+  // U_LF of row `row` of this lane from the nodes of rows row - 1 (S), row
+  // (this one, W/E by shuffle) and row + 1 (N); all lanes take part in the
+  // shuffles, only interior nodes' results are used
+  auto lf = [&](int row, const NodeF64& S, const NodeF64& C, const NodeF64& N, double U[4], double B[4]) {
+    double M1W[4], M2E[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      M1W[cc] = shup(C.M1[cc]);
+      M2E[cc] = shdn(C.M2[cc]);
+    }
+    const double rW = shup(C.u[0]), rE = shdn(C.u[0]);
+    if (colin && row >= 1 && row <= ny - 2) node_lf(C.u, M1W, M2E, S.M3, N.M4, rW, rE, S.u[0], N.u[0], L.ph, alpha, gamma, U, B);
+  };
+
+  // ---- warm-up: rows ra - 2 .. ra + 1, U_LF of ra - 1 and ra, face (ra - 1, ra)
+  NodeF64 nm2, nm1, n0, n1;
+  eval_node(src, plane, off_of(ra - 2), gamma, c1, inv2a, nm2);
+  eval_node(src, plane, off_of(ra - 1), gamma, c1, inv2a, nm1);
+  eval_node(src, plane, off_of(ra), gamma, c1, inv2a, n0);
+  eval_node(src, plane, off_of(ra + 1), gamma, c1, inv2a, n1);
+  double Um[4] = {0, 0, 0, 0}, Bm[4] = {0, 0, 0, 0}, U0[4] = {0, 0, 0, 0}, B0[4] = {0, 0, 0, 0};
+  lf(ra - 1, nm2, nm1, n0, Um, Bm);
+  lf(ra, nm1, n0, n1, U0, B0);
+  double ths, n3[4], eis[4];
+  {
+    double pLr[4], pRr[4], eo[4], no_unused[4];
+    pop(2, ra - 1, pLr);
+    pop(3, ra, pRr);
+    face_f64(nm1.M3, n0.M4, pLr, pRr, is_boundary(c, ra - 1, nx, ny), is_boundary(c, ra, nx, ny), Um, Bm, U0, B0,
+             limiter, ths, eo, eis, n3, no_unused);
+  }
+
+  double lam = 0.0;
+  int flags = 0;
+  for (int q = ra; q <= rb; ++q) {
+    // row q + 2 and U_LF of row q + 1
+    NodeF64 n2;
+    eval_node(src, plane, off_of(q + 2), gamma, c1, inv2a, n2);
+    double U1[4] = {0, 0, 0, 0}, B1[4] = {0, 0, 0, 0};
+    lf(q + 1, n0, n1, n2, U1, B1);
+    const bool bq = is_boundary(c, q, nx, ny);
+    // north face (q, q + 1)
+    double thn, eon[4], ein[4], non[4], nin[4];
+    {
+      double pLr[4], pRr[4];
+      pop(2, q, pLr);
+      pop(3, q + 1, pRr);
+      face_f64(n0.M3, n1.M4, pLr, pRr, bq, is_boundary(c, q + 1, nx, ny), U0, B0, U1, B1, limiter, thn, eon, ein,
+               non, nin);
+    }
+    // east face (c, c + 1) of row q; its data for the west face of lane + 1
+    double the, eoe[4], eie[4], noe[4], nie[4];
+    {
+      double pLr[4], p2[4], Mi[4], pRr[4], UR[4], BR[4];
+      pop(0, q, pLr);
+      pop(1, q, p2);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        Mi[cc] = shdn(n0.M2[cc]);
+        pRr[cc] = shdn(p2[cc]);
+        UR[cc] = shdn(U0[cc]);
+        BR[cc] = shdn(B0[cc]);
+      }
+      face_f64(n0.M1, Mi, pLr, pRr, bq, is_boundary(c + 1, q, nx, ny), U0, B0, UR, BR, limiter, the, eoe, eie, noe,
+               nie);
+    }
+    const double thw = shup(the);
+    double n1w[4], eiw[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      n1w[cc] = shup(noe[cc]);
+      eiw[cc] = shup(eie[cc]);
+    }
+    if (upd) {
+      // Eq. (vlbm5) as written: the new populations, alpha u, and the four
+      // theta-weighted non-equilibrium terms of the cell itself
+      double qn[4];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        double v = n1w[cc] + nie[cc];
+        v = v + n3[cc];
+        v = v + nin[cc];
+        v = v + alpha * n0.u[cc];
+        v = v - thw * eiw[cc];
+        v = v - the * eoe[cc];
+        v = v - ths * eis[cc];
+        v = v - thn * eon[cc];
+        qn[cc] = v;
+      }
+      const size_t off = (size_t)q * nxp + c;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        dst[cc * plane + off] = qn[cc];
+        dst[(size_t)(4 + 0 * 4 + cc) * plane + off] = n1w[cc];
+        dst[(size_t)(4 + 1 * 4 + cc) * plane + off] = nie[cc];
+        dst[(size_t)(4 + 2 * 4 + cc) * plane + off] = n3[cc];
+        dst[(size_t)(4 + 3 * 4 + cc) * plane + off] = nin[cc];
+      }
+      double v1, v2, p;
+      primitive(qn, gamma, v1, v2, p);
+      const bool fin = isfinite(qn[0]) && isfinite(qn[1]) && isfinite(qn[2]) && isfinite(qn[3]);
+      int fl = 0;
+      if (!fin) fl |= 2;
+      if (!(qn[0] > 0.0) || !(p > 0.0)) fl |= 1;
+      if (!fl) {
+        const double l = fmax(fabs(v1), fabs(v2)) + sqrt(gamma * p / qn[0]);
+        lam = fmax(lam, l);
+      }
+      flags |= fl;
+      // zero-gradient copies (outlet column, then the first / last rows)
+      const bool cx = c == nx - 2, cyl = q == 1, cyh = q == ny - 2;
+      if (cx || cyl || cyh) {
+        if (cx) write_equilibrium_node(dst, plane, off + 1, qn, gamma, c1, inv2a);
+        if (cyl) {
+          write_equilibrium_node(dst, plane, off - nxp, qn, gamma, c1, inv2a);
+          if (cx) write_equilibrium_node(dst, plane, off - nxp + 1, qn, gamma, c1, inv2a);
+        }
+        if (cyh) {
+          write_equilibrium_node(dst, plane, off + nxp, qn, gamma, c1, inv2a);
+          if (cx) write_equilibrium_node(dst, plane, off + nxp + 1, qn, gamma, c1, inv2a);
+        }
+      }
+      // inlet column (Dirichlet, every row): written by the first interior column
+      if (c == 1) {
+        const double* inl = D.inlet + (size_t)m * 4 * ny;
+        int rows[3] = {q, -1, -1};
+        if (q == 1) rows[1] = 0;
+        if (q == ny - 2) rows[2] = ny - 1;
+        for (int r = 0; r < 3; ++r) {
+          const int jj = rows[r];
+          if (jj < 0) continue;
+          double qi[4];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) qi[cc] = inl[cc * ny + jj];
+          write_equilibrium_node(dst, plane, (size_t)jj * nxp, qi, gamma, c1, inv2a);
+          double w1, w2, pi;
+          primitive(qi, gamma, w1, w2, pi);
+          lam = fmax(lam, fmax(fabs(w1), fabs(w2)) + sqrt(gamma * pi / qi[0]));
+        }
+      }
+    }
+    // slide the window
+    n0 = n1;
+    n1 = n2;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      U0[cc] = U1[cc];
+      B0[cc] = B1[cc];
+      n3[cc] = non[cc];
+      eis[cc] = ein[cc];
+    }
+    ths = thn;
+  }
+  // lambda >= 0: its FP64 bit pattern orders like an unsigned integer
+  unsigned long long lb = lam_to_bits(lam);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, lb, o);
+    lb = ob > lb ? ob : lb;
+    flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+  }
+  if (lane == 0) {
+    atomicMax(&rs->lam_next_bits, lb);
+    if (flags) atomicOr(&rs->flags, flags);
+  }
+}
+
+// Strips of kFW columns, rows in chunks of kFNW warps with about kFRows rows
+// per warp (fewer, down to 4, when the launch would not give every SM two
+// CTAs); the split changes no result.
+cudaError_t launch_march_f64(const Launch& Lin, cudaStream_t s) {
+  static thread_local Launch L;
+  L = Lin;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int target = kFRows;
+  for (;;) {
+    long long ctas = 0;
+    for (int l = 0; l < L.nlevels; ++l) {
+      const LevelDesc& D = L.lv[l];
+      const int rows = D.ny - 2;
+      ctas += (long long)((D.nx - 2 + kFW - 1) / kFW) * ((rows + kFNW * target - 1) / (kFNW * target));
+    }
+    if (ctas * L.M >= 2LL * sms || target <= 4) break;
+    target = target / 2 < 4 ? 4 : target / 2;
+  }
+  int units = 0;
+  for (int l = 0; l < L.nlevels; ++l) {
+    LevelDesc& D = L.lv[l];
+    const int rows = D.ny - 2;
+    const int chunks = (rows + kFNW * target - 1) / (kFNW * target);
+    D.tiles_x = (D.nx - 2 + kFW - 1) / kFW;
+    D.tiles_y = chunks;
+    D.wrows = (rows + chunks * kFNW - 1) / (chunks * kFNW);
+    D.tile_begin = units;
+    units += D.tiles_x * D.tiles_y;
+  }
+  L.total_tiles = units;
+  step_f64_march_kernel<<<dim3(units, L.M), kFNW * 32, 0, s>>>(L);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t step_f64_smem_bytes() { return sizeof(Smem); }
 
+int f64_variant() {
+  static int v = [] {
+    const char* env = std::getenv("VLBM_F64_VARIANT");
+    return env ? std::atoi(env) : 1;
+  }();
+  return v;
+}
+
+const char* f64_variant_name(int v) { return v == 0 ? "tile32x8" : "march28x4w"; }
+
 cudaError_t launch_step_f64(const Launch& L, cudaStream_t s) {
+  if (f64_variant() != 0) return launch_march_f64(L, s);
   static std::atomic<unsigned long long> configured{0};
   cudaError_t e = once_per_device(configured, [] {
     return cudaFuncSetAttribute(step_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));

@@ -91,15 +91,17 @@ def test_adjoint_full_config_lax_friedrichs_matches_central_differences():
     assert np.abs(grad[:8] - fd).max() <= 1e-5 * np.abs(fd).max(), (grad[:8], fd)
 
 
-def test_adjoint_full_grid_r_theta_matches_reference_adjoint():
+@pytest.mark.parametrize("n,every", [(3, 2), (20, 5)])
+def test_adjoint_full_grid_r_theta_matches_reference_adjoint(n, every):
     # With R-theta the map's derivatives grow without bound at the limiter's
     # kinks within tens of steps (central differences stop meaning the
     # derivative), so the full-size grid is checked against the reference
-    # adjoint itself over a short window: 512 x 256, M = 2, 3 steps.
-    nx, ny, M, n = 512, 256, 2, 3
+    # adjoint itself: 512 x 256, M = 2, over 3 steps and over the first
+    # checkpoint window of the configuration (20 steps, checkpoints every 5).
+    nx, ny, M = 512, 256, 2
     g = np.linspace(0.5, 1.5, nx)
     amp0 = O.Jet().amplitudes().copy()
-    J, grad = gpu_grad(nx, ny, M, n, g, every=2, amp=amp0)
+    J, grad = gpu_grad(nx, ny, M, n, g, every=every, amp=amp0)
     amp = torch.tensor(amp0, requires_grad=True)
     obs = T.axial_mean_density(O.Grid(nx, ny), O.Params(), O.Jet(), 0, M, n, amp)
     (torch.from_numpy(g) * obs).sum().backward()
