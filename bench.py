@@ -467,7 +467,7 @@ def run_ours(args):
         kname = {"tile": "step_mixed_tile_kernel", "pers": "step_mixed_persistent_kernel",
                  "marc": "step_mixed_march_kernel"}.get(design[1][:4], "step_mixed_kernel")
     else:
-        kname = "step_f64_kernel"
+        kname = "step_f64_march_kernel" if design[1].startswith("march") else "step_f64_kernel"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
                 "kernel": kname, "design": design[1], "peak_source": f"{src} hbm_gbs",

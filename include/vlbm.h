@@ -342,12 +342,11 @@ int vlbm_amplitudes(const vlbm_ctx* ctx, double* amp, int* K);
  * bit-identical results; the context picks the fastest by timing each on its
  * first step, unless the environment variable VLBM_MIXED_VARIANT holds a valid
  * index; *index is -1 (and *name "none") before the first step.  An FP64
- * context reports its kernel's design among two (0: 32 x 8 tiles, 1: warps
- * marching up 28-column strips, the default; the environment variable
- * VLBM_F64_VARIANT, read once per process, picks one); both compute identical
- * results.  Any output pointer may be NULL.  No counterpart in the paper,
- * whose update has a single implementation.  Returns VLBM_EINVAL for a NULL
- * ctx. */
+ * context likewise picks among two designs (0: 32 x 8 tiles, 1: warps
+ * marching up 28-column strips; VLBM_F64_VARIANT forces one), which compute
+ * identical results.  Any output pointer may be NULL.  No counterpart in the
+ * paper, whose update has a single implementation.  Returns VLBM_EINVAL for a
+ * NULL ctx. */
 int vlbm_step_design(const vlbm_ctx* ctx, int* index, const char** name, int* count);
 
 /* Failure-detection check of the device waits: runs on the current device

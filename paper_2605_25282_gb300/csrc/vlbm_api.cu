@@ -73,7 +73,7 @@ struct vlbm_ctx {
   double r_jet = 0.05;
   cudaGraphExec_t graph = nullptr;
   bool warmed = false;
-  int variant = -1;  // mixed kernel launch design (index), -1: not tuned yet
+  int variant = -1;  // step kernel launch design (index), -1: not tuned yet
   std::vector<float> tune_ms;  // time per step of every variant when tuned
   std::string err = "no error";
 };
@@ -124,16 +124,27 @@ void release_levels(vlbm_ctx* c) {
   c->warmed = false;
 }
 
-// Picks the mixed kernel's launch design (tile shape, one tile per CTA or
-// persistent) by timing every variant on the live state.  A step launch
-// without the tick that follows it is idempotent: it rewrites the same next
-// lattice and max-reduces the same lambda.  The environment variable
-// VLBM_MIXED_VARIANT (an index) forces a variant.
-int tune_mixed(vlbm_ctx* c) {
+// Launch designs of the context's step kernel: count, and one step launch of
+// design v (no tick).
+int step_designs(const vlbm_ctx* c) { return c->precision == VLBM_FP64 ? f64_variants() : mixed_variants(); }
+cudaError_t launch_design(vlbm_ctx* c, int v) {
+  if (v < 0) v = step_designs(c) - 1;  // not tuned yet: the last design
+  return c->precision == VLBM_FP64 ? launch_step_f64(c->launch, v, c->stream)
+                                   : launch_step_mixed(c->launch, v, c->stream);
+}
+
+// Picks the step kernel's launch design (mixed: tile shapes, persistent CTAs,
+// warp marches; FP64: tiles or the warp march) by timing every design on the
+// live state.  A step launch without the tick that follows it is idempotent:
+// it rewrites the same next lattice and max-reduces the same lambda.  The
+// environment variable VLBM_MIXED_VARIANT / VLBM_F64_VARIANT (an index)
+// forces a design.
+int tune_design(vlbm_ctx* c) {
   if (c->variant >= 0) return VLBM_OK;
-  if (const char* env = std::getenv("VLBM_MIXED_VARIANT")) {
+  const int n = step_designs(c);
+  if (const char* env = std::getenv(c->precision == VLBM_FP64 ? "VLBM_F64_VARIANT" : "VLBM_MIXED_VARIANT")) {
     const int v = std::atoi(env);
-    if (v >= 0 && v < mixed_variants()) {
+    if (v >= 0 && v < n) {
       c->variant = v;
       return VLBM_OK;
     }
@@ -142,12 +153,12 @@ int tune_mixed(vlbm_ctx* c) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(c, VLBM_ECUDA, "cudaEventCreate");
   float best = 1e30f;
-  int best_v = 1;
-  c->tune_ms.assign(mixed_variants(), 0.0f);
-  for (int v = 0; v < mixed_variants(); ++v) {
-    cudaError_t e = launch_step_mixed(c->launch, v, c->stream);
+  int best_v = n - 1;
+  c->tune_ms.assign(n, 0.0f);
+  for (int v = 0; v < n; ++v) {
+    cudaError_t e = launch_design(c, v);
     if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_step_mixed(c->launch, v, c->stream);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_design(c, v);
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0;
@@ -155,7 +166,7 @@ int tune_mixed(vlbm_ctx* c) {
     if (e != cudaSuccess) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      return cuda_fail(c, e, "tuning the mixed kernel");
+      return cuda_fail(c, e, "tuning the step kernel");
     }
     c->tune_ms[v] = ms / 2;
     if (ms < best) {
@@ -170,8 +181,7 @@ int tune_mixed(vlbm_ctx* c) {
 }
 
 int launch_one_step(vlbm_ctx* c) {
-  cudaError_t e = c->precision == VLBM_FP64 ? launch_step_f64(c->launch, c->stream)
-                                             : launch_step_mixed(c->launch, c->variant, c->stream);
+  cudaError_t e = launch_design(c, c->variant);
   if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   e = launch_tick(c->launch, c->precision, 1, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "tick kernel launch");
@@ -205,8 +215,8 @@ int build_graph(vlbm_ctx* c) {
 int run_steps(vlbm_ctx* c, long long n) {
   // the first steps run as plain launches (this also configures the kernels'
   // shared-memory limits before any capture)
-  if (n > 0 && c->precision == VLBM_MIXED) {
-    int st = tune_mixed(c);
+  if (n > 0) {
+    int st = tune_design(c);
     if (st) return st;
   }
   while (n > 0 && !c->warmed) {
@@ -870,6 +880,7 @@ int vlbm_grad_amplitudes(vlbm_ctx* c, int nsteps, int checkpoint_every, const do
   }
   c->prepared = false;
   int stt = prepare(c, std::numeric_limits<double>::infinity());
+  if (stt == VLBM_OK && nsteps > 0) stt = tune_design(c);
   for (long long s = 0; s < nsteps && stt == VLBM_OK && e == cudaSuccess; ++s) {
     if (s % checkpoint_every == 0) save(s, ck + (size_t)(s / checkpoint_every) * sdoubles, ckr + (s / checkpoint_every) * M);
     stt = launch_one_step(c);
@@ -951,17 +962,11 @@ unsigned long long vlbm_kernel_launches(void) { return g_launches.load(); }
 
 int vlbm_step_design(const vlbm_ctx* c, int* index, const char** name, int* count) {
   if (!c) return VLBM_EINVAL;
-  if (c->precision == VLBM_FP64) {
-    const int v = f64_variant();
-    if (index) *index = v;
-    if (name) *name = f64_variant_name(v);
-    if (count) *count = 2;
-    return VLBM_OK;
-  }
   const int v = c->variant;
+  const bool f64 = c->precision == VLBM_FP64;
   if (index) *index = v;
-  if (name) *name = v >= 0 ? mixed_variant_name(v) : "none";
-  if (count) *count = mixed_variants();
+  if (name) *name = v < 0 ? "none" : (f64 ? f64_variant_name(v) : mixed_variant_name(v));
+  if (count) *count = f64 ? f64_variants() : mixed_variants();
   return VLBM_OK;
 }
 

@@ -130,11 +130,10 @@ cudaError_t once_per_device(std::atomic<unsigned long long>& done, F set) {
 }
 
 // Launch helpers implemented in the kernel translation units.
-// FP64 step kernel designs: 0 = 32 x 8 tiles, 1 = warps marching up 28-column
-// strips (default); VLBM_F64_VARIANT (read once per process) picks one.  Both
-// compute identical results.
-cudaError_t launch_step_f64(const Launch& L, cudaStream_t s);
-int f64_variant();
+// FP64 step kernel designs 0..f64_variants()-1: 32 x 8 tiles, warps marching
+// up 28-column strips.  Both compute identical results.
+cudaError_t launch_step_f64(const Launch& L, int variant, cudaStream_t s);
+int f64_variants();
 const char* f64_variant_name(int variant);
 size_t step_f64_smem_bytes();
 void tiles_f64(int nx, int ny, int* tx, int* ty);

@@ -23,7 +23,14 @@ __device__ __forceinline__ double load_sample(const void* p, int is_f32, size_t 
   return is_f32 ? (double)reinterpret_cast<const float*>(p)[idx] : reinterpret_cast<const double*>(p)[idx];
 }
 
-__device__ void bitonic_sort(double* x, int P) {
+// Sorts x[0..P) and y[0..P) ascending together (bitonic network, P a power
+// of two; each stage's P/2 compare-exchanges shared by the threads, thread t
+// taking t, t + blockDim.x, ...).  In a stage of distance j <= 32 the
+// exchanges of a warp stay inside the 64-element blocks of its own indices,
+// so two such stages in a row need only the warp's own ordering; a CTA
+// barrier separates a stage from the next one only when the next reaches
+// further (j > 32), and the sort ends with one.
+__device__ void bitonic_sort2(double* x, double* y, int P) {
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
@@ -35,10 +42,20 @@ __device__ void bitonic_sort(double* x, int P) {
           x[lo] = b;
           x[hi] = a;
         }
+        const double c = y[lo], d = y[hi];
+        if ((c > d) == up) {
+          y[lo] = d;
+          y[hi] = c;
+        }
       }
-      __syncthreads();
+      const int next = j > 1 ? j >> 1 : k;  // the next stage's distance
+      if (next > 32)
+        __syncthreads();
+      else
+        __syncwarp();
     }
   }
+  __syncthreads();
 }
 
 __device__ double block_sum(double v, double* red) {
@@ -97,8 +114,7 @@ __global__ void __launch_bounds__(kStatThreads) stats_kernel(const void* __restr
   const double vA = block_sum(va, red) / (double)M;
   const double vB = block_sum(vb, red) / (double)M;
   __syncthreads();
-  bitonic_sort(xa, P);
-  bitonic_sort(xb, P);
+  bitonic_sort2(xa, xb, P);
   double w = 0.0;
   for (int m = threadIdx.x; m < M; m += blockDim.x) w += fabs(xa[m] - xb[m]);
   const double W = block_sum(w, red) / (double)M;

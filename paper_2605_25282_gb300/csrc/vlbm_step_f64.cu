@@ -16,7 +16,6 @@
 // FP64 is the slow path on GB300 (1/58 of the FP32 rate): this kernel is
 // bound by the FP64 pipe, not by HBM.
 #include <cfloat>
-#include <cstdlib>
 
 #include "vlbm_f64_math.cuh"
 #include "vlbm_internal.cuh"
@@ -705,18 +704,12 @@ cudaError_t launch_march_f64(const Launch& Lin, cudaStream_t s) {
 
 size_t step_f64_smem_bytes() { return sizeof(Smem); }
 
-int f64_variant() {
-  static int v = [] {
-    const char* env = std::getenv("VLBM_F64_VARIANT");
-    return env ? std::atoi(env) : 1;
-  }();
-  return v;
-}
+int f64_variants() { return 2; }
 
-const char* f64_variant_name(int v) { return v == 0 ? "tile32x8" : "march28x4w"; }
+const char* f64_variant_name(int v) { return v == 0 ? "tile32x8" : v == 1 ? "march28x4w" : "?"; }
 
-cudaError_t launch_step_f64(const Launch& L, cudaStream_t s) {
-  if (f64_variant() != 0) return launch_march_f64(L, s);
+cudaError_t launch_step_f64(const Launch& L, int variant, cudaStream_t s) {
+  if (variant != 0) return launch_march_f64(L, s);
   static std::atomic<unsigned long long> configured{0};
   cudaError_t e = once_per_device(configured, [] {
     return cudaFuncSetAttribute(step_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));

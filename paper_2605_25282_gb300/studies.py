@@ -6,6 +6,7 @@ paper's Sec. 3-4 that are more than one bench step.
     python -m paper_2605_25282_gb300.studies cauchy     [--M 64 --times 0.0005,0.001,0.002,0.0035]
     python -m paper_2605_25282_gb300.studies final      [--M 1000 --t 0.0035] [--save state.bin]
     python -m paper_2605_25282_gb300.studies resume     --load state.bin [--M 1000 --steps 200]
+    python -m paper_2605_25282_gb300.studies adjoint    [--M 16 --steps 200]
 
 ladder     one realization per level of the single-realization refinement
            ladder (400x200 ... 5060x2530), fixed steps: cell-updates/s and
@@ -27,6 +28,8 @@ final      the batched ensemble (M = 1000 of 400x200 + 800x400, mixed, one
            then the statistics between the two levels; --save keeps the state.
 resume     a saved state advanced a fixed number of steps (the step kernel on
            the developed, turbulent flow).
+adjoint    the gradient configuration (512x256, checkpoints every 20 steps):
+           time of the amplitude gradient against the forward steps alone.
 
 Every run prints one JSON object.  All inputs are synthetic and seeded
 (Philox4x32-10 KL inlets, seed 0, realizations 0..M-1).
@@ -290,9 +293,36 @@ def resume_steps(load: str, M: int, steps: int, levels=((400, 200), (800, 400)))
     return out
 
 
+def adjoint_timing(nx: int = 512, ny: int = 256, M: int = 16, steps: int = 200, every: int = 20,
+                   limiter: int = 2) -> dict:
+    """The adjoint configuration: the gradient of the axial ensemble-mean density
+    after `steps` FP64 steps with respect to the KL amplitudes (checkpoints every
+    `every` steps), timed against the forward steps alone."""
+    ens = vlbm.Ensemble([(nx, ny)], precision="fp64", relax=vlbm.RelaxParams(limiter=limiter))
+    ens.init(0, M)
+    w = vlbm.axial_weights(ny, nx)
+    ens.grad_amplitudes(2, w, every)  # warm-up (tuning, allocations)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(ens.stream):
+        a.record(ens.stream)
+        J, grad = ens.grad_amplitudes(steps, w, every)
+        b.record(ens.stream)
+    b.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    ens.init(0, M)
+    fwd = _timed_steps(ens, steps)
+    cells = nx * ny * M * steps
+    out = {"study": "adjoint: gradient of the axial ensemble-mean density", "nx": nx, "ny": ny, "M": M,
+           "steps": steps, "checkpoint_every": every, "limiter": limiter, "J": J, "grad": [float(g) for g in grad],
+           "seconds_gradient": sec, "seconds_forward": fwd, "gradient_over_forward": sec / fwd,
+           "forward_GLUPS": cells / fwd / 1e9, "design": ens.step_design()[1]}
+    ens.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("study", choices=["ladder", "precision", "cauchy", "final", "resume"])
+    ap.add_argument("study", choices=["ladder", "precision", "cauchy", "final", "resume", "adjoint"])
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--M", type=int, default=None)
@@ -318,6 +348,8 @@ def main(argv=None):
         res = cauchy(args.M or 64, [float(x) for x in args.times.split(",")], precision=args.precision or "mixed")
     elif args.study == "final":
         res = batched_final_time(args.M or 1000, args.t, save=args.save)
+    elif args.study == "adjoint":
+        res = adjoint_timing(M=args.M or 16, steps=args.steps)
     else:
         res = resume_steps(args.load, args.M or 1000, args.steps)
     print(json.dumps(res), flush=True)
