@@ -56,7 +56,7 @@ NCU_TRAFFIC = {
 # thread operations per SM and clock.  Later in a run the limiter divides and
 # takes pressure roots more often, so over a full run the instructions per
 # cell-update are more and the fraction below is a lower bound.
-FP64_ALU = {"sha": "70c3d6fa0a3e8455+54acf87532a47ae3", "pipe_inst_per_update": 15982684 * 32 / 800000,
+FP64_ALU = {"sha": "909bf072e2e73d0e+54acf87532a47ae3", "pipe_inst_per_update": 15982684 * 32 / 800000,
             "flop_per_update": (165147216 + 159229266 + 2 * 107026840) / 800000, "ops_per_sm_clock": 2,
             "sms": 152}
 
@@ -488,7 +488,8 @@ def run_ours(args):
     stats = {"kernel": "stats_kernel", "ms_per_call": stats_s * 1e3, "bytes_per_call": stats_bytes,
              "achieved_gbs": stats_gbs, "hbm_frac": stats_gbs / hbm if stats_gbs else None,
              "share_of_step": stats_s * 1e3 / (ms / args.steps),
-             "bound": "on-chip sort (two bitonic sorts of the cell's samples in shared memory)",
+             "bound": "FP64 pipe (ncu: 80 % busy with the samples' FP64 conversions, restriction sums and "
+                      "moments; the per-cell sort runs on integer order keys)",
              "sharded": dist is not None}
     if prec == "fp64":
         # bound by the FP64 pipe: the roofline is the ALU one, the HBM figures stay beside it

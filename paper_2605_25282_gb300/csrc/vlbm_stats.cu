@@ -4,7 +4,8 @@
 // One CTA per coarse cell.  The M samples of ensemble a and the M restricted
 // samples of ensemble b (each realization of b block-averaged over its r x r
 // fine cells onto the coarse cell) are gathered into shared memory, padded to
-// a power of two with +inf, bitonic-sorted, and reduced in FP64:
+// a power of two with +inf, bitonic-sorted (as order-preserving integer keys),
+// and reduced in FP64:
 //   mean = sum / M, std = sqrt(sum (x - mean)^2 / M)  (population variance),
 //   W1   = sum_m |a_(m) - b_(m)| / M  over the ascending order statistics.
 // The gather is strided by the field size; consecutive CTAs are neighbouring
@@ -23,6 +24,19 @@ __device__ __forceinline__ double load_sample(const void* p, int is_f32, size_t 
   return is_f32 ? (double)reinterpret_cast<const float*>(p)[idx] : reinterpret_cast<const double*>(p)[idx];
 }
 
+// Order-preserving 64-bit keys of doubles: key(a) < key(b) as unsigned
+// integers exactly when a < b (a non-negative double's bits with the sign bit
+// set; a negative one's bits inverted).  Sorting the keys on the integer ALU
+// sorts the values: GB300 runs FP64 compares on its FP64 pipe (2 operations
+// per SM and clock), integer compares at 64 lanes per SM and clock.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
 // Sorts x[0..P) and y[0..P) ascending together (bitonic network, P a power
 // of two; each stage's P/2 compare-exchanges shared by the threads, thread t
 // taking t, t + blockDim.x, ...).  In a stage of distance j <= 32 the
@@ -30,19 +44,19 @@ __device__ __forceinline__ double load_sample(const void* p, int is_f32, size_t 
 // so two such stages in a row need only the warp's own ordering; a CTA
 // barrier separates a stage from the next one only when the next reaches
 // further (j > 32), and the sort ends with one.
-__device__ void bitonic_sort2(double* x, double* y, int P) {
+__device__ void bitonic_sort2(unsigned long long* x, unsigned long long* y, int P) {
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
         const int lo = 2 * j * (t / j) + (t % j);
         const int hi = lo + j;
         const bool up = (lo & k) == 0;
-        const double a = x[lo], b = x[hi];
+        const unsigned long long a = x[lo], b = x[hi];
         if ((a > b) == up) {
           x[lo] = b;
           x[hi] = a;
         }
-        const double c = y[lo], d = y[hi];
+        const unsigned long long c = y[lo], d = y[hi];
         if ((c > d) == up) {
           y[lo] = d;
           y[hi] = c;
@@ -83,6 +97,10 @@ __global__ void __launch_bounds__(kStatThreads) stats_kernel(const void* __restr
   const size_t na = (size_t)nxa * nya;
   const size_t nb = na * (size_t)r * r;
   const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  // the block mean: a power-of-two block size divides exactly by multiplying
+  const int rr = r * r;
+  const bool rr_pow2 = (rr & (rr - 1)) == 0;
+  const double inv_rr = 1.0 / (double)rr;
   for (int m = threadIdx.x; m < P; m += blockDim.x) {
     if (m < M) {
       xa[m] = load_sample(ens_a, a_f32, (size_t)m * na + cell);
@@ -90,7 +108,7 @@ __global__ void __launch_bounds__(kStatThreads) stats_kernel(const void* __restr
       for (int aa = 0; aa < r; ++aa)
         for (int bb = 0; bb < r; ++bb)
           s += load_sample(ens_b, b_f32, (size_t)m * nb + (size_t)(r * J + aa) * nxb + (size_t)(r * I + bb));
-      xb[m] = s / (double)(r * r);
+      xb[m] = rr_pow2 ? s * inv_rr : s / (double)rr;
     } else {
       xa[m] = inf;
       xb[m] = inf;
@@ -113,10 +131,17 @@ __global__ void __launch_bounds__(kStatThreads) stats_kernel(const void* __restr
   }
   const double vA = block_sum(va, red) / (double)M;
   const double vB = block_sum(vb, red) / (double)M;
+  // sort the samples' order keys in place (each thread converts its own)
+  unsigned long long* ka = reinterpret_cast<unsigned long long*>(xa);
+  unsigned long long* kb = reinterpret_cast<unsigned long long*>(xb);
+  for (int m = threadIdx.x; m < P; m += blockDim.x) {
+    ka[m] = order_key(xa[m]);
+    kb[m] = order_key(xb[m]);
+  }
   __syncthreads();
-  bitonic_sort2(xa, xb, P);
+  bitonic_sort2(ka, kb, P);
   double w = 0.0;
-  for (int m = threadIdx.x; m < M; m += blockDim.x) w += fabs(xa[m] - xb[m]);
+  for (int m = threadIdx.x; m < M; m += blockDim.x) w += fabs(key_value(ka[m]) - key_value(kb[m]));
   const double W = block_sum(w, red) / (double)M;
   if (threadIdx.x == 0) {
     if (mean_a) mean_a[cell] = ma;

@@ -6,7 +6,8 @@ paper's Sec. 3-4 that are more than one bench step.
     python -m paper_2605_25282_gb300.studies cauchy     [--M 64 --times 0.0005,0.001,0.002,0.0035]
     python -m paper_2605_25282_gb300.studies final      [--M 1000 --t 0.0035] [--save state.bin]
     python -m paper_2605_25282_gb300.studies resume     --load state.bin [--M 1000 --steps 200]
-    python -m paper_2605_25282_gb300.studies adjoint    [--M 16 --steps 200]
+    python -m paper_2605_25282_gb300.studies adjoint    [--M 16 --steps 200 --limiter 2]
+    python -m paper_2605_25282_gb300.studies stats      [--M 1000]
 
 ladder     one realization per level of the single-realization refinement
            ladder (400x200 ... 5060x2530), fixed steps: cell-updates/s and
@@ -30,6 +31,8 @@ resume     a saved state advanced a fixed number of steps (the step kernel on
            the developed, turbulent flow).
 adjoint    the gradient configuration (512x256, checkpoints every 20 steps):
            time of the amplitude gradient against the forward steps alone.
+stats      the statistics stage alone on the bench's levels (synthetic
+           lognormal samples): time per call and achieved GB/s.
 
 Every run prints one JSON object.  All inputs are synthetic and seeded
 (Philox4x32-10 KL inlets, seed 0, realizations 0..M-1).
@@ -320,9 +323,32 @@ def adjoint_timing(nx: int = 512, ny: int = 256, M: int = 16, steps: int = 200, 
     return out
 
 
+def stats_timing(M: int = 1000, levels=((400, 200), (800, 400)), reps: int = 10) -> dict:
+    """The statistics stage alone on the bench's levels: restriction of the fine
+    level, per-cell mean, std and sorted one-point W1 over M samples (FP32
+    inputs, lognormal densities around the jet's values), CUDA-event time."""
+    (nxa, nya), (nxb, nyb) = levels
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a = torch.exp(0.3 * torch.randn((M, nya, nxa), device="cuda", generator=g)).float()
+    b = torch.exp(0.3 * torch.randn((M, nyb, nxb), device="cuda", generator=g)).float()
+    for _ in range(3):
+        vlbm.stats_w1_mean_std(a, b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        vlbm.stats_w1_mean_std(a, b)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    r = nxb // nxa
+    nbytes = nxa * nya * (M * 4 * (1 + r * r) + 5 * 8)
+    return {"study": "statistics stage alone", "M": M, "levels": [list(lv) for lv in levels], "ms_per_call": ms,
+            "bytes_per_call": nbytes, "GBs": nbytes / (ms / 1e3) / 1e9}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("study", choices=["ladder", "precision", "cauchy", "final", "resume", "adjoint"])
+    ap.add_argument("study", choices=["ladder", "precision", "cauchy", "final", "resume", "adjoint", "stats"])
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--M", type=int, default=None)
@@ -334,6 +360,7 @@ def main(argv=None):
     ap.add_argument("--levels", type=str, default=None,
                     help="ladder: levels as NXxNY,... (default: the refinement ladder 400x200 ... 5060x2530)")
     ap.add_argument("--warmup", type=int, default=4, help="ladder: untimed steps before the timed ones")
+    ap.add_argument("--limiter", type=int, default=2, help="adjoint: 0 = theta 0 (Lax-Friedrichs), 2 = R-theta")
     ap.add_argument("--control", action="store_true", help="precision: add a perturbed FP64 control run")
     ap.add_argument("--save", type=str, default=None, help="final: write the final state to this file")
     ap.add_argument("--load", type=str, default=None, help="resume: the state file written by final --save")
@@ -349,7 +376,9 @@ def main(argv=None):
     elif args.study == "final":
         res = batched_final_time(args.M or 1000, args.t, save=args.save)
     elif args.study == "adjoint":
-        res = adjoint_timing(M=args.M or 16, steps=args.steps)
+        res = adjoint_timing(M=args.M or 16, steps=args.steps, limiter=args.limiter)
+    elif args.study == "stats":
+        res = stats_timing(M=args.M or 1000)
     else:
         res = resume_steps(args.load, args.M or 1000, args.steps)
     print(json.dumps(res), flush=True)
