@@ -38,26 +38,29 @@ METRIC = "ensemble cell-updates/s (GLUPS) & % HBM roofline, mixed vs FP64, at st
 BYTES_PER_UPDATE = {"mixed": 160, "fp64": 320}
 # DRAM traffic of one step-kernel launch from an ncu capture, with the sha256
 # of the kernel source and the launch design it was taken on (reported as null
-# once either differs).  Mixed: 606.8 MB read + written for the 4.0 M
-# cell-updates of the M = 10 capture (333.4 MB read + 273.4 MB written),
+# once either differs).  Mixed: 606.6 MB read + written for the 4.0 M
+# cell-updates of the M = 10 capture (333.4 MB read + 273.3 MB written),
 # scaled to 400 M cell-updates.
 NCU_TRAFFIC = {
-    "mixed": {"sha": "7dfbe44174883ad5", "design": "march30pf4w", "bytes_per_launch": 60.68e9,
+    "mixed": {"sha": "c22c9559f7eb645c", "design": "march30pf4w", "bytes_per_launch": 60.66e9,
               "capture": "M=10, 400x200 + 800x400, scaled by cell-updates"},
 }
 # The FP64 step kernel is bound by the FP64 pipe, not by HBM.  ncu counters of
-# one launch of the warp-march design (M = 2, 400x200 + 800x400, 800,000
-# cell-updates, the first steps of a run), with the sha256 of the kernel source
-# and of its math header: FP64-pipe warp instructions x 32 per cell-update
-# (every FP64 add, multiply, fused multiply-add, compare, min/max and
-# conversion; the FP64 pipe runs all 32 lanes of a warp instruction), and the
-# FLOPs of its adds, multiplies and fused multiply-adds (165.1 M DADD +
-# 159.2 M DMUL + 107.0 M DFMA thread instructions).  GB300 issues 2 FP64
-# thread operations per SM and clock.  Later in a run the limiter divides and
-# takes pressure roots more often, so over a full run the instructions per
-# cell-update are more and the fraction below is a lower bound.
-FP64_ALU = {"sha": "909bf072e2e73d0e+54acf87532a47ae3", "pipe_inst_per_update": 15982684 * 32 / 800000,
-            "flop_per_update": (165147216 + 159229266 + 2 * 107026840) / 800000, "ops_per_sm_clock": 2,
+# the warp-march design on M = 2 realizations of 400x200 + 800x400 (800,000
+# cell-updates per launch), with the sha256 of the kernel source and of its
+# math header: FP64-pipe warp instructions x 32 per cell-update (every FP64
+# add, multiply, fused multiply-add, compare, min/max and conversion; the FP64
+# pipe runs all 32 lanes of a warp instruction) and the FLOPs of the adds,
+# multiplies and fused multiply-adds, on the first steps of a run (165.1 M
+# DADD + 159.2 M DMUL + 107.0 M DFMA) and on the developed flow at t = 0.002
+# (the limiter divides and takes pressure roots more often there: 170.5 M
+# DADD + 156.9 M DMUL + 75.5 M DFMA).  A full run is mostly developed flow, so
+# the roofline uses the developed count.  GB300 issues 2 FP64 thread
+# operations per SM and clock.
+FP64_ALU = {"sha": "909bf072e2e73d0e+54acf87532a47ae3",
+            "pipe_inst_per_update": 20005234 * 32 / 800000,
+            "pipe_inst_per_update_first_steps": 15982684 * 32 / 800000,
+            "flop_per_update": (170494892 + 156949088 + 2 * 75457984) / 800000, "ops_per_sm_clock": 2,
             "sms": 152}
 
 
@@ -97,6 +100,7 @@ def fp64_alu(glups: float):
     achieved = glups * FP64_ALU["pipe_inst_per_update"]
     return {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "G FP64 inst/s",
             "frac": achieved / peak, "inst_per_cell_update": FP64_ALU["pipe_inst_per_update"],
+            "inst_per_cell_update_first_steps": FP64_ALU["pipe_inst_per_update_first_steps"],
             "flop_per_cell_update": FP64_ALU["flop_per_update"],
             "peak_source": f"{FP64_ALU['sms']} SMs x {FP64_ALU['ops_per_sm_clock']} FP64 ops per clock x "
                            f"{mhz:.0f} MHz (sm_max_mhz)"}

@@ -133,12 +133,17 @@ __device__ __forceinline__ float4 boost(const float4 x, float dw1, float dw2) {
 }
 
 // d_f = [M_out(u_L) - u_out,L] - [M_in(u_R) - u_in,R] = g_in(R) - g_out(L)
-// (g = u_k - M_k), seen in L's frame and in R's frame.
-__device__ __forceinline__ float4 d_in_L(const float4 gL, const float4 gR, float4 PL, float4 PR) {
-  return sub(boost(gR, PL.y - PR.y, PL.z - PR.z), gL);
-}
-__device__ __forceinline__ float4 d_in_R(const float4 gL, const float4 gR, float4 PL, float4 PR) {
-  return sub(gR, boost(gL, PR.y - PL.y, PR.z - PL.z));
+// (g = u_k - M_k), seen in L's frame (gR boosted by w = v_L - v_R) and in R's
+// frame (gL boosted by -w); the two boosts share w and |w|^2 / 2 (the values
+// are those of boost() with each side's own velocity difference, exactly:
+// a - b = -(b - a) in IEEE arithmetic).
+__device__ __forceinline__ void d_in_both(const float4 gL, const float4 gR, const float4 PL, const float4 PR,
+                                          float4& dL, float4& dR) {
+  const float w1 = PL.y - PR.y, w2 = PL.z - PR.z;
+  const float hw = 0.5f * fmaf(w1, w1, w2 * w2);
+  dL = sub(f4(gR.x, fmaf(-w1, gR.x, gR.y), fmaf(-w2, gR.x, gR.z), fmaf(hw, gR.x, gR.w - fmaf(w1, gR.y, w2 * gR.z))),
+           gL);
+  dR = sub(gR, f4(gL.x, fmaf(w1, gL.x, gL.y), fmaf(w2, gL.x, gL.z), fmaf(hw, gL.x, gL.w - fmaf(-w1, gL.y, -w2 * gL.z))));
 }
 
 // The R-theta limit of one side of a face: the largest theta in [0, 1]
@@ -310,8 +315,8 @@ __device__ __forceinline__ float4 a_change_y(const float4 g, const float4 P, flo
 __device__ __forceinline__ float face_theta(const float4 PL, const float4 PR, const float4 gL, const float4 gR,
                                             const float4 UL, const Bnd BL, const float4 UR, const Bnd BR,
                                             bool bL, bool bR, int limiter, const Ctx& k, float4& tdL, float4& tdR) {
-  const float4 dL = d_in_L(gL, gR, PL, PR);
-  const float4 dR = d_in_R(gL, gR, PL, PR);
+  float4 dL, dR;
+  d_in_both(gL, gR, PL, PR, dL, dR);
   float th;
   if (limiter == 0) {
     th = 0.0f;

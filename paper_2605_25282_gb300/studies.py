@@ -237,13 +237,13 @@ def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPE
 
 
 def batched_final_time(M: int = 1000, t: float = 0.0035, levels=((400, 200), (800, 400)),
-                       save: str | None = None) -> dict:
+                       save: str | None = None, precision: str = "mixed") -> dict:
     """The batched ensemble run to the paper's final time: M realizations of
     both levels in one launch per step (mixed, landing on t), then the
     per-cell mean, std and one-point W1 between the levels (the fine level
     restricted onto the coarse grid) and the error functionals."""
     levels = [tuple(lv) for lv in levels]
-    ens = vlbm.Ensemble(levels, precision="mixed")
+    ens = vlbm.Ensemble(levels, precision=precision)
     ens.init(0, M)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(ens.stream):
@@ -263,7 +263,7 @@ def batched_final_time(M: int = 1000, t: float = 0.0035, levels=((400, 200), (80
     b2.synchronize()
     f = _functionals(d0, d1)
     out = {"study": "batched ensemble to the final time", "M": M, "t": t, "levels": [list(lv) for lv in levels],
-           "precision": "mixed", "design": ens.step_design()[1], "seconds": sec, "cell_updates": cells,
+           "precision": precision, "design": ens.step_design()[1], "seconds": sec, "cell_updates": cells,
            "GLUPS": cells / sec / 1e9, "steps": [[int(s.min()), int(s.max())] for s in steps],
            "t_reached": [[float(x.min()), float(x.max())] for x in times],
            "stats_ms": a2.elapsed_time(b2),
@@ -278,11 +278,11 @@ def batched_final_time(M: int = 1000, t: float = 0.0035, levels=((400, 200), (80
     return out
 
 
-def resume_steps(load: str, M: int, steps: int, levels=((400, 200), (800, 400))) -> dict:
-    """Restores a state written by `final --save` (same levels and M, mixed)
+def resume_steps(load: str, M: int, steps: int, levels=((400, 200), (800, 400)), precision: str = "mixed") -> dict:
+    """Restores a state written by `final --save` (same levels, M and precision)
     and advances it `steps` fixed steps: the step kernel on a developed flow."""
     levels = [tuple(lv) for lv in levels]
-    ens = vlbm.Ensemble(levels, precision="mixed")
+    ens = vlbm.Ensemble(levels, precision=precision)
     ens.init(0, M)
     with open(load, "rb") as fh:
         ens.load(fh.read())
@@ -291,7 +291,8 @@ def resume_steps(load: str, M: int, steps: int, levels=((400, 200), (800, 400)))
     cells = sum(nx * ny for nx, ny in levels) * M * steps
     out = {"study": "steps on a restored state", "M": M, "levels": [list(lv) for lv in levels], "steps": steps,
            "t_start": [float(t[0].min()) for t in t0], "seconds": sec, "GLUPS": cells / sec / 1e9,
-           "GBs": cells * BYTES_PER_UPDATE["mixed"] / sec / 1e9, "design": ens.step_design()[1]}
+           "GBs": cells * BYTES_PER_UPDATE[precision] / sec / 1e9, "precision": precision,
+           "design": ens.step_design()[1]}
     ens.close()
     return out
 
@@ -374,13 +375,13 @@ def main(argv=None):
     elif args.study == "cauchy":
         res = cauchy(args.M or 64, [float(x) for x in args.times.split(",")], precision=args.precision or "mixed")
     elif args.study == "final":
-        res = batched_final_time(args.M or 1000, args.t, save=args.save)
+        res = batched_final_time(args.M or 1000, args.t, save=args.save, precision=args.precision or "mixed")
     elif args.study == "adjoint":
         res = adjoint_timing(M=args.M or 16, steps=args.steps, limiter=args.limiter)
     elif args.study == "stats":
         res = stats_timing(M=args.M or 1000)
     else:
-        res = resume_steps(args.load, args.M or 1000, args.steps)
+        res = resume_steps(args.load, args.M or 1000, args.steps, precision=args.precision or "mixed")
     print(json.dumps(res), flush=True)
 
 
