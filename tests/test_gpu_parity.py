@@ -51,9 +51,9 @@ def test_fp64_limiter_modes(limiter):
 
 
 def test_fp64_ragged_tiles_and_levels_in_one_launch():
-    # interior extents that are not multiples of the tile, three levels at once,
-    # including a level with a single interior row
-    levels = [(67, 29), (134, 58), (9, 3)]
+    # interior extents that are not multiples of the tile or of the march's
+    # strips, five levels at once, including single interior rows and columns
+    levels = [(67, 29), (134, 58), (9, 3), (3, 7), (31, 5)]
     M, n = 3, 10
     ens = H.gpu_jet(levels, M)
     ens.step(n)

@@ -18,11 +18,12 @@ SCRIPT = r"""
 import sys, numpy as np
 sys.path.insert(0, {root!r})
 from tests import gpu_helpers as H
-ens = H.gpu_jet([(67, 29), (150, 60), (96, 230)], 3, precision="mixed")
+levels = [(67, 29), (150, 60), (96, 230), (3, 3), (5, 7)]
+ens = H.gpu_jet(levels, 3, precision="mixed")
 ens.step(12)
 idx, name, count = ens.step_design()
 assert idx == {v}, (idx, name)
-np.save({out!r}, np.concatenate([ens.get_state(l)[0].cpu().numpy().ravel() for l in range(3)]))
+np.save({out!r}, np.concatenate([ens.get_state(l)[0].cpu().numpy().ravel() for l in range(len(levels))]))
 """
 
 
@@ -47,7 +48,7 @@ SCRIPT64 = r"""
 import sys, numpy as np
 sys.path.insert(0, {root!r})
 from tests import gpu_helpers as H
-levels = [(67, 29), (150, 60), (96, 230), (9, 3), (31, 5)]
+levels = [(67, 29), (150, 60), (96, 230), (9, 3), (31, 5), (3, 3), (3, 7)]
 for limiter in (2, 0, 1):
     ens = H.gpu_jet(levels, 3, precision="fp64", limiter=limiter)
     ens.step(12 if limiter != 1 else 3)
