@@ -30,3 +30,20 @@ def test_ladders_are_the_configured_grids():
     # the paper's grids have square cells on [0, 2.5] x [-1, 1]
     for nx, ny in studies.LADDER_PAPER:
         assert abs(2.5 / nx - 2.0 / ny) < 1e-15
+
+
+def test_axial_profile_reads_the_head_and_the_axial_spread():
+    # two axis rows of M realizations: jet density 5 +- 0.3 (population std)
+    # upstream of x = 1.5, ambient 0.5 beyond; the head is the last x above 0.55
+    import torch
+
+    nx = 200  # four realizations (the signs below)
+    x = np.arange(nx) * (2.5 / nx)
+    base = np.where(x < 1.5, 5.0, 0.5)
+    sign = np.array([1.0, -1.0, 1.0, -1.0])[:, None, None]
+    rows = base[None, None, :] + 0.3 * sign * (x < 1.4)[None, None, :]
+    axis = torch.tensor(np.repeat(rows, 2, axis=1), dtype=torch.float32)
+    p = studies.axial_profile(axis)
+    assert p["bow_shock_x"] == x[x < 1.5][-1]
+    assert abs(p["axial_std_upstream_median"] - 0.3) < 1e-6
+    assert abs(p["axial_std_peak"] - 0.3) < 1e-6 and p["axial_std_peak_x"] < 1.4
