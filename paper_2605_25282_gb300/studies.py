@@ -3,7 +3,7 @@ paper's Sec. 3-4 that are more than one bench step.
 
     python -m paper_2605_25282_gb300.studies ladder     [--precision fp64|mixed] [--steps 200]
     python -m paper_2605_25282_gb300.studies precision  [--nx 2560 --ny 1280 --M 64 --t 0.0035]
-    python -m paper_2605_25282_gb300.studies cauchy     [--M 64 --times 0.0005,0.001,0.002,0.0035]
+    python -m paper_2605_25282_gb300.studies cauchy     [--M 64 --times 0.0005,0.001,0.002,0.0035] [--batch 64]
     python -m paper_2605_25282_gb300.studies final      [--M 1000 --t 0.0035] [--save state.bin]
     python -m paper_2605_25282_gb300.studies resume     --load state.bin [--M 1000 --steps 200]
     python -m paper_2605_25282_gb300.studies adjoint    [--M 16 --steps 200 --limiter 2]
@@ -165,23 +165,25 @@ def rate(h, err) -> float | None:
     return float(np.polyfit(np.log(h), np.log(err), 1)[0])
 
 
-def _functionals(a: torch.Tensor, b: torch.Tensor, npd: int = 10) -> dict:
+def _functionals(a: torch.Tensor, b: torch.Tensor, npd: int = 10, w12: bool = True) -> dict:
     f = vlbm.stats_error_functionals(a, b)
     e_mean, e_std, w11, e_strong = (float(x) for x in f.cpu())
-    w12, _ = vlbm.stats_w1_two_point(a, b, npd)
-    return {"W_11": w11, "W_12": float(w12), "E_mean": e_mean, "E_std": e_std, "E_strong": e_strong}
+    out = {"W_11": w11, "E_mean": e_mean, "E_std": e_std, "E_strong": e_strong}
+    if w12:
+        out["W_12"] = float(vlbm.stats_w1_two_point(a, b, npd)[0])
+    return out
 
 
-def axial_profile(dens: torch.Tensor, x_max: float = 2.5, rho_amb: float = 0.5) -> dict:
-    """Ensemble statistics of the density on the jet axis (rows ny/2 - 1 and
-    ny/2) of one level [M, ny, nx]: the bow-shock position (the largest x
-    where the axial mean exceeds the ambient density by 10 %), the median
-    axial std upstream of x = 1.4, and the peak axial std with the mean
-    there (the quantities Sec. 4 reads off the axis)."""
-    M, ny, nx = dens.shape
-    st = vlbm.stats_w1_mean_std(dens, dens)
-    mean = (0.5 * (st["mean_a"][ny // 2 - 1] + st["mean_a"][ny // 2])).cpu().numpy()
-    std = (0.5 * (st["std_a"][ny // 2 - 1] + st["std_a"][ny // 2])).cpu().numpy()
+def axial_profile(axis: torch.Tensor, x_max: float = 2.5, rho_amb: float = 0.5) -> dict:
+    """Ensemble statistics of the density on the jet axis of one level, from
+    its two rows next to y = 0 ([M, 2, nx]): the bow-shock position (the
+    largest x where the axial mean exceeds the ambient density by 10 %), the
+    median axial std upstream of x = 1.4, and the peak axial std with the mean
+    there (the quantities Sec. 4 reads off the axis); population std."""
+    M, _, nx = axis.shape
+    a = axis.double()
+    mean = a.mean(0).mean(0).cpu().numpy()
+    std = a.std(0, unbiased=False).mean(0).cpu().numpy()
     x = np.arange(nx) * (x_max / nx)
     above = np.nonzero(mean > 1.1 * rho_amb)[0]
     k = int(np.argmax(std))
@@ -190,49 +192,70 @@ def axial_profile(dens: torch.Tensor, x_max: float = 2.5, rho_amb: float = 0.5) 
             "axial_std_peak": float(std[k]), "axial_std_peak_x": float(x[k]), "axial_mean_at_peak": float(mean[k])}
 
 
-def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPER, precision: str = "mixed") -> dict:
+def cauchy(M: int = 64, times=(0.0005, 0.001, 0.002, 0.0035), levels=LADDER_PAPER, precision: str = "mixed",
+           batch: int | None = None, w12: bool = True) -> dict:
     """The paper's protocol (Sec. 3.3-3.4): every level's density restricted
     onto the coarsest grid, the Cauchy comparison of successive levels and the
-    reference comparison against the finest, rates by Eq. (ratefit)."""
-    ens = vlbm.Ensemble(levels, precision=precision)
-    ens.init(0, M)
+    reference comparison against the finest, rates by Eq. (ratefit).  The M
+    realizations run in batches of `batch` (realizations b .. b + batch - 1
+    of the same seeded sequence, all four levels in one launch per step); the
+    restricted densities and the axis rows of every batch are kept in host
+    memory and the functionals are taken over all M at the end.  W_12 (an
+    exact M-point assignment per point pair) is skipped with w12 False."""
+    batch = min(batch or M, M)
     nx0, ny0 = levels[0]
+    T, NL = len(times), len(levels)
+    keep = {(ti, l): [] for ti in range(T) for l in range(NL)}
+    axis_rows = {(ti, l): [] for ti in range(T) for l in range(NL)}
+    secs = [0.0] * T
+    steps = [[None] * NL for _ in range(T)]
+    for b0 in range(0, M, batch):
+        mb = min(batch, M - b0)
+        ens = vlbm.Ensemble(levels, precision=precision)
+        ens.init(0, mb, m_begin=b0)
+        for ti, t in enumerate(times):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(ens.stream):
+                a.record(ens.stream)
+                ens.advance_to(t)
+                b.record(ens.stream)
+            b.synchronize()
+            secs[ti] += a.elapsed_time(b) / 1e3
+            for l, (nx, ny) in enumerate(levels):
+                s_l = ens.time(l)[1]
+                lo, hi = int(s_l.min()), int(s_l.max())
+                prev = steps[ti][l]
+                steps[ti][l] = [lo, hi] if prev is None else [min(prev[0], lo), max(prev[1], hi)]
+                # the binding orders the caller's current stream after the
+                # ensemble's work; restriction then runs on that stream
+                d = ens.density(l, f32=False)
+                axis_rows[(ti, l)].append(d[:, ny // 2 - 1: ny // 2 + 1].float().cpu())
+                c = vlbm.stats_restrict(d, nx // nx0) if nx != nx0 else d
+                keep[(ti, l)].append(c.cpu())
+                del d, c
+        ens.close()
     out = {"study": "Cauchy and reference convergence on the paper's ladder", "domain": "[0, 2.5] x [-1, 1]",
-           "M": M, "precision": precision, "levels": [list(lv) for lv in levels],
+           "M": M, "batch": batch, "precision": precision, "levels": [list(lv) for lv in levels],
            "common_grid": [nx0, ny0], "snapshots": []}
-    keys = ("W_11", "W_12", "E_mean", "E_std", "E_strong")
-    for t in times:
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(ens.stream):
-            a.record(ens.stream)
-            ens.advance_to(t)
-            b.record(ens.stream)
-        b.synchronize()
-        sec = a.elapsed_time(b) / 1e3
-        steps = [ens.time(l)[1] for l in range(len(levels))]
-        # the binding orders the caller's current stream after the ensemble's
-        # work; restriction and functionals then run on that stream
-        common, axis = [], []
-        for l, (nx, ny) in enumerate(levels):
-            d = ens.density(l, f32=False)
-            axis.append(axial_profile(d))
-            common.append(vlbm.stats_restrict(d, nx // nx0) if nx != nx0 else d)
-            del d
-        snap = {"t": t, "seconds": sec, "steps": [[int(s.min()), int(s.max())] for s in steps],
-                "axis": axis, "cauchy": [], "reference": []}
-        L = len(levels) - 1
+    keys = ("W_11", "W_12", "E_mean", "E_std", "E_strong") if w12 else ("W_11", "E_mean", "E_std", "E_strong")
+    L = NL - 1
+    dx = [2.5 / nx for nx, _ in levels]
+    for ti, t in enumerate(times):
+        common = [torch.cat(keep[(ti, l)]).cuda() for l in range(NL)]
+        axis = [axial_profile(torch.cat(axis_rows[(ti, l)])) for l in range(NL)]
+        snap = {"t": t, "seconds": secs[ti], "steps": steps[ti], "axis": axis, "cauchy": [], "reference": []}
         for l in range(1, L + 1):
-            snap["cauchy"].append({"pair": [levels[l - 1][0], levels[l][0]], **_functionals(common[l - 1], common[l])})
+            snap["cauchy"].append({"pair": [levels[l - 1][0], levels[l][0]],
+                                   **_functionals(common[l - 1], common[l], w12=w12)})
         for l in range(L):
-            snap["reference"].append({"pair": [levels[l][0], levels[L][0]], **_functionals(common[l], common[L])})
-        dx = [2.5 / nx for nx, _ in levels]
+            snap["reference"].append({"pair": [levels[l][0], levels[L][0]],
+                                      **_functionals(common[l], common[L], w12=w12)})
         snap["rates"] = {
             "cauchy": {k: rate(dx[:L], [p[k] for p in snap["cauchy"]]) for k in keys},
             "reference": {k: rate(dx[:L], [p[k] for p in snap["reference"]]) for k in keys},
         }
         out["snapshots"].append(snap)
         del common
-    ens.close()
     return out
 
 
@@ -362,6 +385,8 @@ def main(argv=None):
                     help="ladder: levels as NXxNY,... (default: the refinement ladder 400x200 ... 5060x2530)")
     ap.add_argument("--warmup", type=int, default=4, help="ladder: untimed steps before the timed ones")
     ap.add_argument("--limiter", type=int, default=2, help="adjoint: 0 = theta 0 (Lax-Friedrichs), 2 = R-theta")
+    ap.add_argument("--batch", type=int, default=None, help="cauchy: realizations per batch (default: all at once)")
+    ap.add_argument("--no-w12", action="store_true", help="cauchy: skip the two-point distance W_12")
     ap.add_argument("--control", action="store_true", help="precision: add a perturbed FP64 control run")
     ap.add_argument("--save", type=str, default=None, help="final: write the final state to this file")
     ap.add_argument("--load", type=str, default=None, help="resume: the state file written by final --save")
@@ -373,7 +398,8 @@ def main(argv=None):
     elif args.study == "precision":
         res = precision_study(args.nx, args.ny, args.M or 64, args.t, args.control)
     elif args.study == "cauchy":
-        res = cauchy(args.M or 64, [float(x) for x in args.times.split(",")], precision=args.precision or "mixed")
+        res = cauchy(args.M or 64, [float(x) for x in args.times.split(",")], precision=args.precision or "mixed",
+                     batch=args.batch, w12=not args.no_w12)
     elif args.study == "final":
         res = batched_final_time(args.M or 1000, args.t, save=args.save, precision=args.precision or "mixed")
     elif args.study == "adjoint":
