@@ -358,8 +358,8 @@ __device__ __forceinline__ float face_theta(const float4 PL, const float4 PR, co
 // The kept Maxwellians and the cell's parts are fetched through src.mk(k) and
 // src.g(k) where they are used (k = 0..3), which keeps them out of registers
 // until then.
-template <class Src>
-__device__ __forceinline__ float4 update_cell(float4* __restrict__ dst, size_t plane, size_t off, const float4 Pc,
+template <class Src, class I>
+__device__ __forceinline__ float4 update_cell(float4* __restrict__ dst, I plane, I off, const float4 Pc,
                                               const float4 ULF, float thW, const float4 tdRW, float thE,
                                               const float4 tdLE, float thS, const float4 tdRS, float thN,
                                               const float4 tdLN, const Src& src, const Ctx& k, float& lam,
@@ -406,7 +406,8 @@ __device__ __forceinline__ float4 update_cell(float4* __restrict__ dst, size_t p
 // equilibrium populations (g' = 0) into the outlet column and the first / last
 // rows next to it, and, in the first interior column, the inlet datum of its
 // row (and of the corner rows) as FP32 primitives with equilibrium populations.
-__device__ __forceinline__ void boundary_writes(float4* __restrict__ dst, size_t plane, size_t off, int gi, int gj,
+template <class I>
+__device__ __forceinline__ void boundary_writes(float4* __restrict__ dst, I plane, I off, int gi, int gj,
                                                 int nx, int ny, int nxp, const float4 Pn,
                                                 const float4* __restrict__ inl, const Ctx& k, float& lam) {
   const bool cxl = gi == nx - 2, cyl = gj == 1, cyh = gj == ny - 2;
@@ -416,8 +417,9 @@ __device__ __forceinline__ void boundary_writes(float4* __restrict__ dst, size_t
     for (int t = 0; t < 5; ++t) {
       const bool on = t == 0 ? cxl : t == 1 ? cyl : t == 2 ? (cyl && cxl) : t == 3 ? cyh : (cyh && cxl);
       if (!on) continue;
-      const long long dj = t == 0 ? 0 : (t <= 2 ? -(long long)nxp : (long long)nxp);
-      const size_t o = off + dj + (t == 0 || t == 2 || t == 4 ? 1 : 0);
+      // the row below (t = 1, 2) wraps around in unsigned index arithmetic
+      const I dj = t == 0 ? I(0) : (t <= 2 ? I(0) - I(nxp) : I(nxp));
+      const I o = off + dj + I(t == 0 || t == 2 || t == 4 ? 1 : 0);
       dst[o] = Pn;
 #pragma unroll
       for (int q = 1; q <= 4; ++q) dst[q * plane + o] = f4(0.f, 0.f, 0.f, 0.f);
@@ -430,7 +432,7 @@ __device__ __forceinline__ void boundary_writes(float4* __restrict__ dst, size_t
       const int jj = r == 0 ? gj : r == 1 ? (gj == 1 ? 0 : -1) : (gj == ny - 2 ? ny - 1 : -1);
       if (jj < 0) continue;
       const float4 Pi = inl[jj];
-      const size_t oi = (size_t)jj * nxp;
+      const I oi = I(jj) * I(nxp);
       dst[oi] = Pi;
 #pragma unroll
       for (int q = 1; q <= 4; ++q) dst[q * plane + oi] = f4(0.f, 0.f, 0.f, 0.f);
@@ -779,7 +781,10 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
   if (ra > rb) return;
   // lane l holds column x0 - 1 + l of the strip starting at x0 = 1 + kMW * strip
   const int c = (unit % D.tiles_x) * kMW + lane;
-  const size_t plane = D.plane;
+  // element offsets within one realization's lattice fit in 32 bits (the
+  // launcher checks 5 planes < 2^31), which keeps the per-row address
+  // arithmetic in 32-bit integers
+  const int plane = (int)D.plane;
   const int par = (int)(rs->steps & 1);
   const float4* __restrict__ src =
       reinterpret_cast<const float4*>(D.lat) + ((size_t)par * L.M + m) * D.real_stride;
@@ -795,10 +800,10 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
   const int cf = lane == 0 ? c - 1 : c + 1;  // the halo lanes' far column
   const bool far = (lane == 0 || lane == 31) && cf >= 0 && cf <= nx - 1;
   const float4 z4 = f4(0.f, 0.f, 0.f, 0.f);
-  auto ldP = [&](int q) { return q >= 0 && q <= ny - 1 ? __ldg(src + (size_t)q * nxp + cl) : z4; };
-  auto ldF = [&](int q) { return far && q >= 0 && q <= ny - 1 ? __ldg(src + (size_t)q * nxp + cf) : z4; };
+  auto ldP = [&](int q) { return q >= 0 && q <= ny - 1 ? __ldg(src + (q * nxp + cl)) : z4; };
+  auto ldF = [&](int q) { return far && q >= 0 && q <= ny - 1 ? __ldg(src + (q * nxp + cf)) : z4; };
   auto ldG = [&](int kk, int q) {
-    return q >= 0 && q <= ny - 1 ? __ldg(src + (size_t)(kk + 1) * plane + (size_t)q * nxp + cl) : z4;
+    return q >= 0 && q <= ny - 1 ? __ldg(src + ((kk + 1) * plane + q * nxp + cl)) : z4;
   };
   auto inner = [&](int q) { return colin && q >= 1 && q <= ny - 2; };
   auto west = [&](const float4 P, const float4 F) {
@@ -852,11 +857,12 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
   auto prefetch = [&](int q) {
     float4(&r)[6][kMNW][32] = ring[q & 1];
     const bool v2 = q + 2 <= ny - 1;
-    cp_async16(&r[0][wid][lane], src + (size_t)(v2 ? q + 2 : 0) * nxp + cl, v2);
-    cp_async16(&r[1][wid][lane], src + (size_t)(v2 ? q + 2 : 0) * nxp + (far ? cf : cl), v2 && far);
+    const int row2 = (v2 ? q + 2 : 0) * nxp, row0 = q * nxp + cl;
+    cp_async16(&r[0][wid][lane], src + (row2 + cl), v2);
+    cp_async16(&r[1][wid][lane], src + (row2 + (far ? cf : cl)), v2 && far);
 #pragma unroll
-    for (int kk = 0; kk < 3; ++kk) cp_async16(&r[2 + kk][wid][lane], src + (size_t)(kk + 1) * plane + (size_t)q * nxp + cl, true);
-    cp_async16(&r[5][wid][lane], src + (size_t)4 * plane + (size_t)(q + 1) * nxp + cl, true);
+    for (int kk = 0; kk < 3; ++kk) cp_async16(&r[2 + kk][wid][lane], src + ((kk + 1) * plane + row0), true);
+    cp_async16(&r[5][wid][lane], src + (4 * plane + nxp + row0), true);
   };
   if (PF) {
     prefetch(ra);
@@ -921,7 +927,7 @@ __global__ void __launch_bounds__(kMNW * 32, MINB) step_mixed_march_kernel(const
         __device__ float4 mk(int i) const { return mk_[i][wid][lane]; }
         __device__ float4 g(int i) const { return i == 0 ? g0 : i == 1 ? g1 : i == 2 ? g2 : g3; }
       } cell{smk[q & 1], wid, lane, G1, G2, G3, g4q};
-      const size_t off = (size_t)q * nxp + c;
+      const int off = q * nxp + c;
       const float4 Pn =
           update_cell(dst, plane, off, Pq, Uq, thW, tdRW, thE, tdLE, thS, tdRS, thN, tdLN, cell, k, lam, flags);
       boundary_writes(dst, plane, off, c, q, nx, ny, nxp, Pn, inl, k, lam);
@@ -1053,6 +1059,10 @@ cudaError_t launch_persistent(Launch& L, cudaStream_t s) {
 // split does not change any result.
 template <int MINB, bool PF>
 cudaError_t launch_march(Launch& L, cudaStream_t s) {
+  // the march indexes a realization's five planes with 32-bit offsets; a
+  // level beyond that (over 429 M nodes) runs on the tile design instead
+  for (int l = 0; l < L.nlevels; ++l)
+    if (5 * L.lv[l].plane >= ((size_t)1 << 31)) return launch_tile<8>(L, s);
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int target = kMarchRows;
