@@ -349,6 +349,15 @@ int vlbm_amplitudes(const vlbm_ctx* ctx, double* amp, int* K);
  * NULL ctx. */
 int vlbm_step_design(const vlbm_ctx* ctx, int* index, const char** name, int* count);
 
+/* Rows per warp of the mixed warp-march design in use (*rows = 0 for the
+ * other designs, for FP64 contexts and before the first step).  A march splits each level into strips
+ * of columns, one warp per strip and chunk of rows; the split changes no
+ * result.  On a small launch (a single small grid) the context times several
+ * row counts on its first step and keeps the fastest; the environment
+ * variable VLBM_MARCH_ROWS (> 0) forces the count of a mixed march.  No
+ * counterpart in the paper.  Returns VLBM_EINVAL for a NULL ctx or rows. */
+int vlbm_step_rows(const vlbm_ctx* ctx, int* rows);
+
 /* Failure-detection check of the device waits: runs on the current device
  * one mbarrier wait that nothing completes, bounded by limit_s seconds
  * (0 < limit_s <= 10) as every wait of the step kernels is bounded, and

@@ -122,6 +122,7 @@ void release_levels(vlbm_ctx* c) {
     c->graph = nullptr;
   }
   c->warmed = false;
+  c->variant = -1;  // a new ensemble size is tuned again
 }
 
 // Launch designs of the context's step kernel: count, and one step launch of
@@ -136,13 +137,21 @@ cudaError_t launch_design(vlbm_ctx* c, int v) {
 // Picks the step kernel's launch design (mixed: tile shapes, persistent CTAs,
 // warp marches; FP64: tiles or the warp march) by timing every design on the
 // live state.  A step launch without the tick that follows it is idempotent:
-// it rewrites the same next lattice and max-reduces the same lambda.  The
-// environment variable VLBM_MIXED_VARIANT / VLBM_F64_VARIANT (an index)
-// forces a design.
+// it rewrites the same next lattice and max-reduces the same lambda.  On a
+// small mixed launch (under four rounds of resident CTAs: a single small
+// grid) each design is timed over more launches and every warp march also at
+// several rows per warp: fewer rows give more CTAs and a shorter march each
+// but re-evaluate more halo rows.  The environment variable
+// VLBM_MIXED_VARIANT / VLBM_F64_VARIANT (an index) forces a design (no
+// timing), VLBM_MARCH_ROWS the rows per warp of a mixed march.
 int tune_design(vlbm_ctx* c) {
   if (c->variant >= 0) return VLBM_OK;
   const int n = step_designs(c);
-  if (const char* env = std::getenv(c->precision == VLBM_FP64 ? "VLBM_F64_VARIANT" : "VLBM_MIXED_VARIANT")) {
+  const bool mixed = c->precision == VLBM_MIXED;
+  c->launch.march_rows = 0;
+  const char* env_rows = mixed ? std::getenv("VLBM_MARCH_ROWS") : nullptr;
+  if (env_rows && std::atoi(env_rows) > 0) c->launch.march_rows = std::atoi(env_rows);
+  if (const char* env = std::getenv(mixed ? "VLBM_MIXED_VARIANT" : "VLBM_F64_VARIANT")) {
     const int v = std::atoi(env);
     if (v >= 0 && v < n) {
       c->variant = v;
@@ -152,30 +161,51 @@ int tune_design(vlbm_ctx* c) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(c, VLBM_ECUDA, "cudaEventCreate");
-  float best = 1e30f;
-  int best_v = n - 1;
-  c->tune_ms.assign(n, 0.0f);
-  for (int v = 0; v < n; ++v) {
+  // time per launch of design v over `reps` launches after an untimed one
+  auto time_design = [&](int v, int reps, float& ms) {
     cudaError_t e = launch_design(c, v);
     if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = launch_design(c, v);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_design(c, v);
     if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return cuda_fail(c, e, "tuning the step kernel");
-    }
-    c->tune_ms[v] = ms / 2;
-    if (ms < best) {
-      best = ms;
-      best_v = v;
+    ms /= reps;
+    return e;
+  };
+  // a small launch (under four rounds of resident CTAs for the march rule) is
+  // timed over more launches, and a march there over several row counts
+  const bool tune_rows = mixed && c->launch.march_rows == 0;
+  bool small = false;
+  for (int v = 0; v < n && mixed; ++v) {
+    const double w = mixed_march_waves(c->launch, v, 0);
+    small = small || (w > 0.0 && w < 4.0);
+  }
+  const int reps = small ? 16 : 2;
+  static const int kRows[] = {0, 1, 2, 3, 4, 6, 8, 12, 16};  // 0: the launcher's rule
+  float best = 1e30f;
+  int best_v = n - 1, best_rows = c->launch.march_rows;
+  c->tune_ms.assign(n, 0.0f);
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < n && e == cudaSuccess; ++v) {
+    const bool rows_too = tune_rows && small && mixed_march_rows(c->launch, v) > 0;
+    for (int r : kRows) {
+      if (r != 0 && !rows_too) break;
+      if (tune_rows) c->launch.march_rows = r;
+      float ms = 0;
+      e = time_design(v, reps, ms);
+      if (e != cudaSuccess) break;
+      if (r == 0) c->tune_ms[v] = ms;
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+        best_rows = c->launch.march_rows;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  c->launch.march_rows = e == cudaSuccess ? best_rows : 0;
+  if (e != cudaSuccess) return cuda_fail(c, e, "tuning the step kernel");
   c->variant = best_v;
   return VLBM_OK;
 }
@@ -364,7 +394,9 @@ int init_impl(vlbm_ctx* c, uint64_t seed, int m_begin, int M, const vlbm_perturb
   }
   // launch descriptor
   Launch& L = c->launch;
+  const int rows = L.march_rows;  // tuned for this ensemble size (0 after release_levels)
   L = Launch{};
+  L.march_rows = c->variant >= 0 ? rows : 0;
   L.ph = c->ph;
   L.pf.gamma = (float)c->ph.gamma;
   L.pf.gm1 = (float)(c->ph.gamma - 1.0);
@@ -959,6 +991,13 @@ int vlbm_check_bounded_wait(double limit_s) {
 }
 
 unsigned long long vlbm_kernel_launches(void) { return g_launches.load(); }
+
+int vlbm_step_rows(const vlbm_ctx* c, int* rows) {
+  if (!c || !rows) return VLBM_EINVAL;
+  const int v = c->variant;
+  *rows = v < 0 || c->precision == VLBM_FP64 ? 0 : mixed_march_rows(c->launch, v);
+  return VLBM_OK;
+}
 
 int vlbm_step_design(const vlbm_ctx* c, int* index, const char** name, int* count) {
   if (!c) return VLBM_EINVAL;

@@ -83,6 +83,7 @@ struct Launch {
   int nlevels;
   int M;
   int total_tiles;
+  int march_rows;  // rows per warp of the mixed warp-march designs (0: the launcher's rule)
   LevelDesc lv[kMaxLevels];
   // TMA descriptors of the mixed kernel, filled per launch for the tile shape
   // in use: nodal-state boxes (radius-2 halo) and non-equilibrium boxes
@@ -143,6 +144,11 @@ void tiles_f64(int nx, int ny, int* tx, int* ty);
 // marching up column strips.  All compute bit-identical results.
 int mixed_variants();
 const char* mixed_variant_name(int variant);
+// For the warp-march designs: the rows per warp a launch of L uses
+// (L.march_rows, or the launcher's rule when 0), and the CTAs of that launch
+// over the CTAs the GPU holds at once; 0 for the other designs.
+int mixed_march_rows(const Launch& L, int variant);
+double mixed_march_waves(const Launch& L, int variant, int rows);
 // Fills the tile decomposition and TMA descriptors of `variant` into a copy of
 // L and launches; returns cudaErrorNotSupported if the driver lacks TMA encode.
 cudaError_t launch_step_mixed(const Launch& L, int variant, cudaStream_t s);

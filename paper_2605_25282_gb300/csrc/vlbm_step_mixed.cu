@@ -1052,30 +1052,45 @@ cudaError_t launch_persistent(Launch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+int sm_count() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+// CTAs of one realization's launch (all levels) with `rows` rows per warp.
+long long march_ctas(const Launch& L, int rows) {
+  long long ctas = 0;
+  for (int l = 0; l < L.nlevels; ++l) {
+    const LevelDesc& D = L.lv[l];
+    const int r = D.ny - 2;
+    ctas += (long long)((D.nx - 2 + kMW - 1) / kMW) * ((r + kMNW * rows - 1) / (kMNW * rows));
+  }
+  return ctas;
+}
+
+// Rows per warp: L.march_rows when set; else kMarchRows, fewer (down to 4)
+// when the launch would not give every SM two rounds of MINB CTAs (a single
+// small grid): each warp then re-evaluates one more halo row per fewer rows,
+// but the GPU fills.  The split does not change any result; the context's
+// tuning times other counts on small launches.
+int march_rows_for(const Launch& L, int minb) {
+  if (L.march_rows > 0) return L.march_rows;
+  const long long slots = (long long)sm_count() * minb;
+  int target = kMarchRows;
+  while (march_ctas(L, target) * L.M < 2 * slots && target > 4) target = target / 2 < 4 ? 4 : target / 2;
+  return target;
+}
+
 // Strips of kMW columns; rows split into chunks of kMNW warps with about
-// kMarchRows rows per warp, fewer (down to 4) when the launch would not give
-// every SM two rounds of MINB CTAs (a single small grid): each warp then
-// re-evaluates one more halo row per fewer rows, but the GPU fills.  The
-// split does not change any result.
+// march_rows_for rows per warp.
 template <int MINB, bool PF>
 cudaError_t launch_march(Launch& L, cudaStream_t s) {
   // the march indexes a realization's five planes with 32-bit offsets; a
   // level beyond that (over 429 M nodes) runs on the tile design instead
   for (int l = 0; l < L.nlevels; ++l)
     if (5 * L.lv[l].plane >= ((size_t)1 << 31)) return launch_tile<8>(L, s);
-  int dev = 0, sms = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int target = kMarchRows;
-  for (;;) {
-    long long ctas = 0;
-    for (int l = 0; l < L.nlevels; ++l) {
-      const LevelDesc& D = L.lv[l];
-      const int rows = D.ny - 2;
-      ctas += (long long)((D.nx - 2 + kMW - 1) / kMW) * ((rows + kMNW * target - 1) / (kMNW * target));
-    }
-    if (ctas * L.M >= 2LL * sms * MINB || target <= 4) break;
-    target = target / 2 < 4 ? 4 : target / 2;
-  }
+  const int target = march_rows_for(L, MINB);
   int units = 0;
   for (int l = 0; l < L.nlevels; ++l) {
     LevelDesc& D = L.lv[l];
@@ -1093,9 +1108,20 @@ cudaError_t launch_march(Launch& L, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// CTAs per SM of the march designs 3..6 (register bound MINB)
+int march_minb(int v) { return v == 4 || v == 6 ? 5 : 4; }
+
 }  // namespace
 
 int mixed_variants() { return kNumVariants; }
+int mixed_march_rows(const Launch& L, int v) { return v >= 3 && v < kNumVariants ? march_rows_for(L, march_minb(v)) : 0; }
+double mixed_march_waves(const Launch& L, int v, int rows) {
+  if (v < 3 || v >= kNumVariants) return 0.0;
+  Launch c = L;
+  c.march_rows = rows;
+  const int r = march_rows_for(c, march_minb(v));
+  return (double)march_ctas(c, r) * L.M / ((double)sm_count() * march_minb(v));
+}
 const char* mixed_variant_name(int v) { return v >= 0 && v < kNumVariants ? kVariantNames[v] : "?"; }
 
 cudaError_t launch_step_mixed(const Launch& Lin, int variant, cudaStream_t s) {

@@ -76,7 +76,8 @@ def ladder(precision: str = "fp64", steps: int = 200, warmup: int = 4, levels=LA
         cells = nx * ny * M * steps
         gbs = cells * BYTES_PER_UPDATE[precision] / sec / 1e9
         row = {"nx": nx, "ny": ny, "GLUPS": cells / sec / 1e9, "GBs": gbs, "ms_per_step": sec * 1e3 / steps,
-               "state_MB": 2 * nx * ny * M * BYTES_PER_UPDATE[precision] / 2 / 1e6}
+               "state_MB": 2 * nx * ny * M * BYTES_PER_UPDATE[precision] / 2 / 1e6,
+               "design": ens.step_design()[1], "rows_per_warp": ens.step_rows()}
         if peak_gbs:
             row["hbm_frac"] = gbs / peak_gbs
         # levels whose state fits in L2 (129 MB) are not HBM measurements

@@ -32,7 +32,8 @@ EXPORTED = [
     "vlbm_advance_to", "vlbm_moments", "vlbm_density", "vlbm_time", "vlbm_sync", "vlbm_get_state",
     "vlbm_set_state", "stats_w1_mean_std", "stats_error_functionals", "stats_error_functionals_noalloc",
     "stats_quantiles", "stats_histogram", "stats_restrict", "stats_w1_two_point",
-    "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_step_design", "vlbm_grad_amplitudes", "vlbm_amplitudes",
+    "vlbm_save", "vlbm_load", "vlbm_last_error", "vlbm_step_design", "vlbm_step_rows", "vlbm_grad_amplitudes",
+    "vlbm_amplitudes",
     "vlbm_check_bounded_wait", "vlbm_destroy",
 ]
 
@@ -111,6 +112,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "vlbm_load": ([p, p, ctypes.c_size_t], i),
         "vlbm_last_error": ([p], ctypes.c_char_p),
         "vlbm_step_design": ([p, p, ctypes.POINTER(ctypes.c_char_p), p], i),
+        "vlbm_step_rows": ([p, p], i),
         "vlbm_grad_amplitudes": ([p, i, i, p, p, p], i),
         "vlbm_amplitudes": ([p, p, p], i),
         "vlbm_check_bounded_wait": ([d], i),
@@ -349,6 +351,13 @@ class Ensemble:
         idx, cnt, name = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_char_p()
         _check(self.lib.vlbm_step_design(self.ctx, ctypes.byref(idx), ctypes.byref(name), ctypes.byref(cnt)), self.ctx)
         return idx.value, name.value.decode(), cnt.value
+
+    def step_rows(self) -> int:
+        """Rows per warp of the mixed warp-march design in use (0 for the
+        other designs, for FP64 and before the first step)."""
+        rows = ctypes.c_int(0)
+        _check(self.lib.vlbm_step_rows(self.ctx, ctypes.byref(rows)), self.ctx)
+        return rows.value
 
     def get_state(self, level: int = 0, m0: int = 0, count: int | None = None, pops: bool = True):
         count = self._count(m0, count)

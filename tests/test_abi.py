@@ -94,6 +94,8 @@ def test_null_context_calls_fail_cleanly():
     assert lib.vlbm_step(None, 1) == 1
     assert lib.vlbm_advance_to(None, 0.1) == 1
     assert lib.vlbm_sync(None) == 1
+    rows = ctypes.c_int(5)
+    assert lib.vlbm_step_rows(None, ctypes.byref(rows)) == 1 and rows.value == 5
     assert lib.vlbm_last_error(None)
     lib.vlbm_destroy(None)
 
@@ -117,6 +119,9 @@ def test_init_samples_rejects_out_of_range_host_values_before_device_work():
         idx, name, cnt = ctypes.c_int(7), ctypes.c_char_p(), ctypes.c_int(0)
         assert lib.vlbm_step_design(ctx, ctypes.byref(idx), ctypes.byref(name), ctypes.byref(cnt)) == 0
         assert idx.value == -1 and name.value == b"none" and cnt.value >= 5
+        rows = ctypes.c_int(7)
+        assert lib.vlbm_step_rows(ctx, ctypes.byref(rows)) == 0 and rows.value == 0
+        assert lib.vlbm_step_rows(ctx, None) == 1
     finally:
         lib.vlbm_destroy(ctx)
 
