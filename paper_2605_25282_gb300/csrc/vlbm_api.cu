@@ -138,10 +138,10 @@ cudaError_t launch_design(vlbm_ctx* c, int v) {
 // warp marches; FP64: tiles or the warp march) by timing every design on the
 // live state.  A step launch without the tick that follows it is idempotent:
 // it rewrites the same next lattice and max-reduces the same lambda.  On a
-// small mixed launch (under four rounds of resident CTAs: a single small
-// grid) each design is timed over more launches and every warp march also at
-// several rows per warp: fewer rows give more CTAs and a shorter march each
-// but re-evaluate more halo rows.  The environment variable
+// mixed launch that does not fill the GPU once (a single small grid) each
+// design is timed over more launches and every warp march also at several
+// rows per warp: fewer rows give more CTAs and a shorter march each but
+// re-evaluate more halo rows.  The environment variable
 // VLBM_MIXED_VARIANT / VLBM_F64_VARIANT (an index) forces a design (no
 // timing), VLBM_MARCH_ROWS the rows per warp of a mixed march.
 int tune_design(vlbm_ctx* c) {
@@ -172,13 +172,15 @@ int tune_design(vlbm_ctx* c) {
     ms /= reps;
     return e;
   };
-  // a small launch (under four rounds of resident CTAs for the march rule) is
-  // timed over more launches, and a march there over several row counts
+  // a launch that does not fill the GPU once with the march rule's rows (a
+  // single small grid) is timed over more launches, and a march there over
+  // several row counts; larger launches keep the rule, whose rows suit the
+  // developed flow as well as the first step that the tuning sees
   const bool tune_rows = mixed && c->launch.march_rows == 0;
   bool small = false;
   for (int v = 0; v < n && mixed; ++v) {
     const double w = mixed_march_waves(c->launch, v, 0);
-    small = small || (w > 0.0 && w < 4.0);
+    small = small || (w > 0.0 && w < 1.0);
   }
   const int reps = small ? 16 : 2;
   static const int kRows[] = {0, 1, 2, 3, 4, 6, 8, 12, 16};  // 0: the launcher's rule
