@@ -51,16 +51,16 @@ NCU_TRAFFIC = {
 # math header: FP64-pipe warp instructions x 32 per cell-update (every FP64
 # add, multiply, fused multiply-add, compare, min/max and conversion; the FP64
 # pipe runs all 32 lanes of a warp instruction) and the FLOPs of the adds,
-# multiplies and fused multiply-adds, on the first steps of a run (165.1 M
-# DADD + 159.2 M DMUL + 107.0 M DFMA) and on the developed flow at t = 0.002
-# (the limiter divides and takes pressure roots more often there: 170.5 M
-# DADD + 156.9 M DMUL + 75.5 M DFMA).  A full run is mostly developed flow, so
-# the roofline uses the developed count.  GB300 issues 2 FP64 thread
-# operations per SM and clock.
-FP64_ALU = {"sha": "909bf072e2e73d0e+54acf87532a47ae3",
-            "pipe_inst_per_update": 20005234 * 32 / 800000,
-            "pipe_inst_per_update_first_steps": 15982684 * 32 / 800000,
-            "flop_per_update": (170494892 + 156949088 + 2 * 75457984) / 800000, "ops_per_sm_clock": 2,
+# multiplies and fused multiply-adds, on the first steps of a run (151.0 M
+# DADD + 149.5 M DMUL + 108.9 M DFMA) and on the developed flow at t = 0.002
+# (157.4 M DADD + 146.5 M DMUL + 73.2 M DFMA).  A full run is mostly developed
+# flow, so the roofline uses the developed count.  GB300 issues 2 FP64 thread
+# operations per SM and clock (152 x 2 x 2 x 2.07 GHz = 1.26 TFLOP/s, GB300's
+# nominal FP64 rate).
+FP64_ALU = {"sha": "24e738279663953b+ce7574c07d3d6886",
+            "pipe_inst_per_update": 15484412 * 32 / 800000,
+            "pipe_inst_per_update_first_steps": 15645124 * 32 / 800000,
+            "flop_per_update": (157408760 + 146507958 + 2 * 73170058) / 800000, "ops_per_sm_clock": 2,
             "sms": 152}
 
 

@@ -30,34 +30,71 @@ __device__ __forceinline__ void fluxes(const double q[4], double gamma, double f
 
 // Largest theta in [0, 1] keeping U0 + theta D inside the admissible,
 // relaxed-bounded set (convex: the feasible thetas form [0, theta*]); the
-// pressure floor enters as kk = eps_p / (gamma - 1).
-static __device__ double theta_star_kk(const double U0[4], const double D[4], double lo_b, double hi_b,
-                                       double eps_r, double kk) {
-  // The density limits num / den lower theta only when num < den (a correctly
-  // rounded quotient of num >= den > 0 is >= 1), so the division runs only
-  // then: the same result as dividing always, for every input.
-  double th = 1.0;
+// pressure floor enters as kk = eps_p / (gamma - 1).  theta_star_kk composes
+// the parts below in this order: the density limit (theta_pre, a division
+// where it binds, theta_density), the pressure test q(th) >= 0 with
+// q(theta) = A theta^2 + B theta + C (C = q(0) = theta_c of the node), and
+// where it fails the root (theta_root).  A kernel that evaluates many sides
+// at once may take their divisions and roots together; every part is the
+// same arithmetic, so the result is the same.
+
+// q(0) of a node: U0's pressure function rho E - |m|^2 / 2 - kk rho.
+__device__ __forceinline__ double theta_c(const double U0[4], double kk) {
+  return U0[0] * U0[3] - 0.5 * (U0[1] * U0[1] + U0[2] * U0[2]) - kk * U0[0];
+}
+
+// The density limit num / den of one side (a division only where it binds:
+// num < den; a correctly rounded quotient of num >= den > 0 is >= 1, so the
+// result is the same as dividing always) and the coefficients A, B of q.
+struct ThetaPre {
+  double num, den, A, B;
+  bool divide;
+};
+__device__ __forceinline__ void theta_pre(const double U0[4], const double D[4], double lo_b, double hi_b,
+                                          double eps_r, double kk, ThetaPre& t) {
   const double lower = eps_r > lo_b ? eps_r : lo_b;
+  t.divide = false;
+  t.num = 0.0;
+  t.den = 1.0;
   if (D[0] < 0.0) {
-    const double num = U0[0] - lower;
-    if (num < -D[0]) {
-      const double lim = num / (-D[0]);
-      if (lim < th) th = lim;
-    }
+    t.num = U0[0] - lower;
+    t.den = -D[0];
+    t.divide = t.num < t.den;
   } else if (D[0] > 0.0) {
-    const double num = hi_b - U0[0];
-    if (num < D[0]) {
-      const double lim = num / D[0];
-      if (lim < th) th = lim;
-    }
+    t.num = hi_b - U0[0];
+    t.den = D[0];
+    t.divide = t.num < t.den;
   }
+  t.B = U0[0] * D[3] + D[0] * U0[3] - (U0[1] * D[1] + U0[2] * D[2]) - kk * D[0];
+  t.A = D[0] * D[3] - 0.5 * (D[1] * D[1] + D[2] * D[2]);
+}
+
+// theta after the density limit: 1, or the quotient lim where it is smaller;
+// never below 0.
+__device__ __forceinline__ double theta_density(bool divided, double lim) {
+  double th = 1.0;
+  if (divided && lim < th) th = lim;
   if (th < 0.0) th = 0.0;
-  const double C = U0[0] * U0[3] - 0.5 * (U0[1] * U0[1] + U0[2] * U0[2]) - kk * U0[0];
-  const double B = U0[0] * D[3] + D[0] * U0[3] - (U0[1] * D[1] + U0[2] * D[2]) - kk * D[0];
-  const double A = D[0] * D[3] - 0.5 * (D[1] * D[1] + D[2] * D[2]);
+  return th;
+}
+
+// The pressure test at th: true with the final theta in *out when q(th) >= 0
+// (th) or C <= 0 (0); false when the root of q below th is needed.
+__device__ __forceinline__ bool theta_final(double th, double A, double B, double C, double* out) {
   const double qth = C + th * (B + th * A);
-  if (qth >= 0.0) return th;
-  if (C <= 0.0) return 0.0;
+  if (qth >= 0.0) {
+    *out = th;
+    return true;
+  }
+  if (C <= 0.0) {
+    *out = 0.0;
+    return true;
+  }
+  return false;
+}
+
+// The smallest positive root of q (C > 0 > q(th)), clamped to [0, th].
+__device__ __forceinline__ double theta_root(double A, double B, double C, double th) {
   double r;
   if (A == 0.0) {
     r = -C / B;
@@ -77,6 +114,17 @@ static __device__ double theta_star_kk(const double U0[4], const double D[4], do
   if (r > th) r = th;
   if (r < 0.0) r = 0.0;
   return r;
+}
+
+static __device__ double theta_star_kk(const double U0[4], const double D[4], double lo_b, double hi_b,
+                                       double eps_r, double kk) {
+  ThetaPre t;
+  theta_pre(U0, D, lo_b, hi_b, eps_r, kk, t);
+  const double th = theta_density(t.divide, t.divide ? t.num / t.den : 0.0);
+  const double C = theta_c(U0, kk);
+  double out;
+  if (theta_final(th, t.A, t.B, C, &out)) return out;
+  return theta_root(t.A, t.B, C, th);
 }
 
 static __device__ double theta_star(const double U0[4], const double D[4], double lo_b, double hi_b,

@@ -460,8 +460,41 @@ __device__ __forceinline__ void face_f64(const double Mo[4], const double Mi[4],
 __device__ __forceinline__ double shup(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ double shdn(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 
+// The limiter's sides of one warp and row (north face L, R; east face L, R):
+// their density-limit quotients num / den, the coefficients A, B, C of the
+// pressure function, theta before the root, and the results; `items` lists
+// the pending sides (side * 32 + lane) of one stage.
+struct SideSlots {
+  double num[4][32], den[4][32], A[4][32], B[4][32], C[4][32], th[4][32], res[4][32];
+  int items[128];
+};
+
+// The FP64 pipe executes every lane of a warp instruction, so a division or a
+// root that one lane of a warp needs costs the whole warp; evaluated side by
+// side, a row pays for up to four of each.  Here the lanes queue the sides
+// that need one (pend[s]) and the warp evaluates the queue, one side per lane:
+// one pass for up to 32 sides.  root = false: res = num / den; root = true:
+// res = theta_root(A, B, C, th).
+__device__ __forceinline__ void warp_queue_eval(SideSlots& S, const bool pend[4], int lane, bool root) {
+  const unsigned lt = (1u << lane) - 1u;
+  int n = 0;
+#pragma unroll
+  for (int sd = 0; sd < 4; ++sd) {
+    const unsigned mk = __ballot_sync(0xffffffffu, pend[sd]);
+    if (pend[sd]) S.items[n + __popc(mk & lt)] = sd * 32 + lane;
+    n += __popc(mk);
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) {
+    const int it = S.items[i], sd = it >> 5, l = it & 31;
+    S.res[sd][l] = root ? theta_root(S.A[sd][l], S.B[sd][l], S.C[sd][l], S.th[sd][l]) : S.num[sd][l] / S.den[sd][l];
+  }
+  __syncwarp();
+}
+
 // blockIdx.x = (strip, row chunk) over all levels, blockIdx.y = realization.
 __global__ void __launch_bounds__(kFNW * 32, 1) step_f64_march_kernel(const Launch L) {
+  __shared__ SideSlots slots[kFNW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int unit = blockIdx.x, lvl = 0;
   while (lvl + 1 < L.nlevels && unit >= L.lv[lvl + 1].tile_begin) ++lvl;
@@ -538,30 +571,95 @@ __global__ void __launch_bounds__(kFNW * 32, 1) step_f64_march_kernel(const Laun
     double U1[4] = {0, 0, 0, 0}, B1[4] = {0, 0, 0, 0};
     lf(q + 1, n0, n1, n2, U1, B1);
     const bool bq = is_boundary(c, q, nx, ny);
-    // north face (q, q + 1)
+    const bool bn = is_boundary(c, q + 1, nx, ny), be = is_boundary(c + 1, q, nx, ny);
+    // north face (q, q + 1) and east face (c, c + 1) of row q (its data for
+    // the west face of lane + 1): the non-equilibrium terms eo = Mo - pL,
+    // ei = Mi - pR (a boundary node's populations stand in by its
+    // equilibria), theta_f, and the streamed populations no, ni
     double thn, eon[4], ein[4], non[4], nin[4];
-    {
-      double pLr[4], pRr[4];
-      pop(2, q, pLr);
-      pop(3, q + 1, pRr);
-      face_f64(n0.M3, n1.M4, pLr, pRr, bq, is_boundary(c, q + 1, nx, ny), U0, B0, U1, B1, limiter, thn, eon, ein,
-               non, nin);
-    }
-    // east face (c, c + 1) of row q; its data for the west face of lane + 1
     double the, eoe[4], eie[4], noe[4], nie[4];
+    double MiE[4];
     {
-      double pLr[4], p2[4], Mi[4], pRr[4], UR[4], BR[4];
-      pop(0, q, pLr);
+      double pN[4], pNr[4], pE[4], p2[4], pEr[4];
+      pop(2, q, pN);
+      pop(3, q + 1, pNr);
+      pop(0, q, pE);
       pop(1, q, p2);
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
-        Mi[cc] = shdn(n0.M2[cc]);
-        pRr[cc] = shdn(p2[cc]);
+        MiE[cc] = shdn(n0.M2[cc]);
+        pEr[cc] = shdn(p2[cc]);
+        const double pl = bq ? n0.M3[cc] : pN[cc], pr = bn ? n1.M4[cc] : pNr[cc];
+        const double ple = bq ? n0.M1[cc] : pE[cc], pre = be ? MiE[cc] : pEr[cc];
+        eon[cc] = n0.M3[cc] - pl;
+        ein[cc] = n1.M4[cc] - pr;
+        eoe[cc] = n0.M1[cc] - ple;
+        eie[cc] = MiE[cc] - pre;
+      }
+    }
+    {
+      double UR[4], BR[4];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
         UR[cc] = shdn(U0[cc]);
         BR[cc] = shdn(B0[cc]);
       }
-      face_f64(n0.M1, Mi, pLr, pRr, bq, is_boundary(c + 1, q, nx, ny), U0, B0, UR, BR, limiter, the, eoe, eie, noe,
-               nie);
+      const bool upd_e = __shfl_down_sync(0xffffffffu, upd, 1) && lane < 31;
+      thn = (bq && bn) || limiter == 0 ? 0.0 : 1.0;
+      the = (bq && be) || limiter == 0 ? 0.0 : 1.0;
+      if (limiter == 2) {
+        // sides: 0 north L (this node), 1 north R (row q + 1), 2 east L (this
+        // node), 3 east R (lane + 1); a face no updated cell uses is skipped
+        SideSlots& S = slots[wid];
+        const bool needN = upd && !(bq && bn), needE = (upd || upd_e) && !(bq && be);
+        const bool act[4] = {needN && !bq, needN && !bn, needE && !bq, needE && !be};
+        bool pend[4];
+        {
+          const double C0 = theta_c(U0, B0[3]);
+          const double Cs[4] = {C0, theta_c(U1, B1[3]), C0, shdn(C0)};
+#pragma unroll
+          for (int sd = 0; sd < 4; ++sd) {
+            const double* U = sd == 0 || sd == 2 ? U0 : (sd == 1 ? U1 : UR);
+            const double* B = sd == 0 || sd == 2 ? B0 : (sd == 1 ? B1 : BR);
+            const double sg = sd == 0 || sd == 2 ? -4.0 : 4.0;
+            double DD[4];
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) DD[cc] = sg * (sd < 2 ? eon[cc] - ein[cc] : eoe[cc] - eie[cc]);
+            ThetaPre t;
+            theta_pre(U, DD, B[0], B[1], B[2], B[3], t);
+            S.num[sd][lane] = t.num;
+            S.den[sd][lane] = t.den;
+            S.A[sd][lane] = t.A;
+            S.B[sd][lane] = t.B;
+            S.C[sd][lane] = Cs[sd];
+            pend[sd] = act[sd] && t.divide;
+          }
+        }
+        warp_queue_eval(S, pend, lane, false);
+        double t[4];
+#pragma unroll
+        for (int sd = 0; sd < 4; ++sd) {
+          const double th = theta_density(pend[sd], pend[sd] ? S.res[sd][lane] : 0.0);
+          t[sd] = 1.0;
+          const bool fin = !act[sd] || theta_final(th, S.A[sd][lane], S.B[sd][lane], S.C[sd][lane], &t[sd]);
+          S.th[sd][lane] = th;
+          pend[sd] = !fin;
+        }
+        __syncwarp();
+        warp_queue_eval(S, pend, lane, true);
+#pragma unroll
+        for (int sd = 0; sd < 4; ++sd)
+          if (pend[sd]) t[sd] = S.res[sd][lane];
+        if (needN) thn = t[0] < t[1] ? t[0] : t[1];
+        if (needE) the = t[2] < t[3] ? t[2] : t[3];
+      }
+    }
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      non[cc] = n0.M3[cc] + thn * eon[cc];
+      nin[cc] = n1.M4[cc] + thn * ein[cc];
+      noe[cc] = n0.M1[cc] + the * eoe[cc];
+      nie[cc] = MiE[cc] + the * eie[cc];
     }
     const double thw = shup(the);
     double n1w[4], eiw[4];
