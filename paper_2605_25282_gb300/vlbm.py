@@ -346,8 +346,8 @@ class Ensemble:
         return J.value, grad
 
     def step_design(self):
-        """(index, name, count) of the mixed step kernel's launch design; index
-        -1 before the first step or for FP64."""
+        """(index, name, count) of the step kernel's launch design (mixed or
+        FP64); index -1 before the first step."""
         idx, cnt, name = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_char_p()
         _check(self.lib.vlbm_step_design(self.ctx, ctypes.byref(idx), ctypes.byref(name), ctypes.byref(cnt)), self.ctx)
         return idx.value, name.value.decode(), cnt.value

@@ -66,8 +66,13 @@ def test_fp64_ragged_tiles_and_levels_in_one_launch():
         assert np.allclose(t, ref["t"], rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("design", [0, 1])
 @pytest.mark.parametrize("limiter,rough", [(2, 0.3), (0, 0.3), (1, 0.0), (2, 0.0)])
-def test_fp64_random_states(limiter, rough):
+def test_fp64_random_states(limiter, rough, design, monkeypatch):
+    # both FP64 designs (0: tiles, 1: warp march, whose limiter queues the
+    # divisions and roots of a row for the warp: on the rough states most
+    # sides need both, more than one pass of 32); 45 columns are two strips
+    monkeypatch.setenv("VLBM_F64_VARIANT", str(design))
     nx, ny, M = 45, 37, 2
     seed = 11
     g = O.Grid(nx, ny)
@@ -81,6 +86,7 @@ def test_fp64_random_states(limiter, rough):
     ens.set_state(torch.tensor(np.stack(us)), torch.tensor(np.stack(ps)))
     nsteps = 3
     ens.step(nsteps)
+    assert ens.step_design()[0] == design
     ug, pg = map(H.to_np, ens.get_state(0))
     for m in range(M):
         inl = O.inlet(g, P, O.Jet(), seed, m)
