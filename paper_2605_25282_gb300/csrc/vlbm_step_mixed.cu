@@ -117,14 +117,6 @@ __device__ __forceinline__ float4 axpy(float s, float4 x, float4 y) {
   return cat4(__ffma2_rn(ss, lo2(x), lo2(y)), __ffma2_rn(ss, hi2(x), hi2(y)));
 }
 
-// Boosted lab fluxes B_w f(u) = f(u') + w1 u' and B_w g(u) = g(u') + w2 u'.
-__device__ __forceinline__ float4 xflux(const float4 u, float d1, float d2, float p, float w1) {
-  return f4(fmaf(w1, u.x, u.y), fmaf(w1, u.y, fmaf(u.y, d1, p)), fmaf(w1, u.z, u.y * d2), fmaf(w1, u.w, (u.w + p) * d1));
-}
-__device__ __forceinline__ float4 yflux(const float4 u, float d1, float d2, float p, float w2) {
-  return f4(fmaf(w2, u.x, u.z), fmaf(w2, u.y, u.y * d2), fmaf(w2, u.z, fmaf(u.z, d2, p)), fmaf(w2, u.w, (u.w + p) * d2));
-}
-
 // Boost of a rest-frame vector x by dw = w_new - w_old.
 __device__ __forceinline__ float4 boost(const float4 x, float dw1, float dw2) {
   const float m1 = fmaf(-dw1, x.x, x.y), m2 = fmaf(-dw2, x.x, x.z);
@@ -185,7 +177,8 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 __device__ __forceinline__ float side_root(float th, float A, float Bq, float C) {
   const float sq = sqrt_approx(fmaxf(fmaf(Bq, Bq, -4.0f * (A * C)), 0.0f));
   const float Q = -0.5f * (Bq + copysignf(sq, Bq));
-  const float r = Q > 0.0f ? __fdividef(C, Q) : __fdividef(Q, A);
+  const bool qp = Q > 0.0f;
+  const float r = __fdividef(qp ? C : Q, qp ? Q : A);
   return C > 0.0f ? fminf(fmaxf(r, 0.0f), th) : 0.0f;
 }
 
@@ -384,19 +377,24 @@ __device__ __forceinline__ float4 update_cell(float4* __restrict__ dst, I plane,
   // g_k^{n+1} = M_k(u_X) - theta_f g_k(X) - M_k(u^{n+1}), X the upwind node,
   // formed in the cell's old frame and boosted once to the new one.  In that
   // frame B g_1(W) = g_2(c) - d_W (the face's d seen by c), and likewise for
-  // the other three faces.
+  // the other three faces.  The new state's Maxwellians in the old frame take
+  // the factored form of the neighbours' (maxwellian_in_frame) with the new
+  // state's relative velocity dv and lab velocity wn:
+  //   M_1,2 = (rho s, rho s dv1 +- hp, rho s dv2, E' s +- hp dv1),
+  //   s = c1 +- h wn1 (M_3,4 likewise with the y components), E' = U.w.
   const float dw1 = wn1 - Pc.y, dw2 = wn2 - Pc.z;
-  const float4 cU = scale(k.c1, U);
-  const float4 Fx = scale(k.h, xflux(U, dv1, dv2, pn, Pc.y));
-  const float4 Fy = scale(k.h, yflux(U, dv1, dv2, pn, Pc.z));
+  const float hp = k.h * pn, hpx = hp * dv1, hpy = hp * dv2;
+  const float s1 = fmaf(k.h, wn1, k.c1), s2 = fmaf(-k.h, wn1, k.c1);
+  const float s3 = fmaf(k.h, wn2, k.c1), s4 = fmaf(-k.h, wn2, k.c1);
+  const float r1 = rn * s1, r2 = rn * s2, r3 = rn * s3, r4 = rn * s4;
   float4 X;
-  X = add(axpy(-thW, src.g(1), sub(src.mk(0), add(cU, Fx))), tdRW);
+  X = add(axpy(-thW, src.g(1), sub(src.mk(0), f4(r1, fmaf(r1, dv1, hp), r1 * dv2, fmaf(U.w, s1, hpx)))), tdRW);
   dst[1 * plane + off] = boost(X, dw1, dw2);
-  X = sub(axpy(-thE, src.g(0), sub(src.mk(1), sub(cU, Fx))), tdLE);
+  X = sub(axpy(-thE, src.g(0), sub(src.mk(1), f4(r2, fmaf(r2, dv1, -hp), r2 * dv2, fmaf(U.w, s2, -hpx)))), tdLE);
   dst[2 * plane + off] = boost(X, dw1, dw2);
-  X = add(axpy(-thS, src.g(3), sub(src.mk(2), add(cU, Fy))), tdRS);
+  X = add(axpy(-thS, src.g(3), sub(src.mk(2), f4(r3, r3 * dv1, fmaf(r3, dv2, hp), fmaf(U.w, s3, hpy)))), tdRS);
   dst[3 * plane + off] = boost(X, dw1, dw2);
-  X = sub(axpy(-thN, src.g(2), sub(src.mk(3), sub(cU, Fy))), tdLN);
+  X = sub(axpy(-thN, src.g(2), sub(src.mk(3), f4(r4, r4 * dv1, fmaf(r4, dv2, -hp), fmaf(U.w, s4, -hpy)))), tdLN);
   dst[4 * plane + off] = boost(X, dw1, dw2);
   return Pn;
 }

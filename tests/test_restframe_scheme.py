@@ -97,6 +97,48 @@ def test_boost_identities():
     assert np.allclose(flux_in_frame(cb, d1, d2, P[:, 3], w2, 1), boost(g, w1, w2), rtol=1e-12, atol=1e-10)
 
 
+def factored_maxwellian(P, w1, w2, k, c1, h, gamma=GAMMA):
+    """B_w M_k(u) in the mixed kernel's factored form, from the node's
+    primitives P = (rho, v1, v2, p) and the frame velocity w: with d = v - w,
+    s = c1 +- h v_dir (+ for k = 1, 3), hp = +- h p and E' = rho |d|^2 / 2 +
+    p / (gamma - 1): (rho s, rho s d1 [+ hp], rho s d2 [+ hp], E' s + hp d_dir),
+    the hp term in the direction's momentum."""
+    rho, v1, v2, p = P.T
+    d1, d2 = v1 - w1, v2 - w2
+    sg = 1.0 if k in (1, 3) else -1.0
+    vdir, ddir = (v1, d1) if k in (1, 2) else (v2, d2)
+    s = c1 + sg * h * vdir
+    hp = sg * h * p
+    Ep = 0.5 * rho * (d1 * d1 + d2 * d2) + p / (gamma - 1.0)
+    rs = rho * s
+    m1 = rs * d1 + (hp if k in (1, 2) else 0.0)
+    m2 = rs * d2 + (hp if k in (3, 4) else 0.0)
+    return np.stack([rs, m1, m2, Ep * s + hp * ddir], axis=-1)
+
+
+def test_factored_maxwellians_are_boosted_lab_maxwellians():
+    # the form both the neighbours' and the new state's Maxwellians take in
+    # the kernel: B_w M_k(u) with M_1,2 = c1 u +- f(u) / 2a, M_3,4 = c1 u +- g(u) / 2a
+    rng = np.random.default_rng(5)
+    n = 200
+    rho = rng.uniform(0.2, 5, n)
+    v1, v2 = rng.normal(0, 300, n), rng.normal(0, 3, n)
+    p = rng.uniform(0.01, 2, n)
+    u = np.stack([rho, rho * v1, rho * v2, p * RG + 0.5 * rho * (v1 ** 2 + v2 ** 2)], axis=-1)
+    w1, w2 = v1 + rng.normal(0, 2, n), v2 + rng.normal(0, 2, n)
+    a = 2.0 * (np.abs(v1).max() + 10.0)
+    c1, h = 0.25, 0.5 / a
+    f, g = lab_flux(u)
+    P = np.stack([rho, v1, v2, p], axis=-1)
+    for k, lab in ((1, c1 * u + h * f), (2, c1 * u - h * f), (3, c1 * u + h * g), (4, c1 * u - h * g)):
+        ref = boost(lab, w1, w2)
+        got = factored_maxwellian(P, w1, w2, k, c1, h)
+        # the reference boosts lab vectors of the jet's speeds: its own
+        # rounding is that of the lab values (the kernel's reason for the form)
+        scale = np.abs(lab).max(axis=0)
+        assert (np.abs(got - ref) / scale).max() < 1e-14, k
+
+
 # ---- the rest-frame step -----------------------------------------------------
 
 class RestFrameJet:
