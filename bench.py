@@ -38,11 +38,11 @@ METRIC = "ensemble cell-updates/s (GLUPS) & % HBM roofline, mixed vs FP64, at st
 BYTES_PER_UPDATE = {"mixed": 160, "fp64": 320}
 # DRAM traffic of one step-kernel launch from an ncu capture, with the sha256
 # of the kernel source and the launch design it was taken on (reported as null
-# once either differs).  Mixed: 606.7 MB read + written for the 4.0 M
-# cell-updates of the M = 10 capture (333.3 MB read + 273.3 MB written),
+# once either differs).  Mixed: 607.0 MB read + written for the 4.0 M
+# cell-updates of the M = 10 capture (333.3 MB read + 273.6 MB written),
 # scaled to 400 M cell-updates.
 NCU_TRAFFIC = {
-    "mixed": {"sha": "899964e9d1d2a5f1", "design": "march30pf4w", "bytes_per_launch": 60.67e9,
+    "mixed": {"sha": "0d90d89fd786c14a", "design": "march30pf4w", "bytes_per_launch": 60.70e9,
               "capture": "M=10, 400x200 + 800x400, scaled by cell-updates"},
 }
 # The FP64 step kernel is bound by the FP64 pipe, not by HBM.  ncu counters of

@@ -12,9 +12,9 @@ Short horizon, per cell.  Two effects set the bound:
     ambient gas sits beside a moving stream, that is a few 1e-4 of p.
 Hence rho and v within 1e-4 (v relative to |v1| + |v2| + c) and p within
 1e-3.  Measured on GB300 after 10 steps of the 200 x 100 jet, M = 4: rho
-4.6e-6, v 4.5e-5, p 4.8e-4 with R-theta (the floor margin and the shear
+4.3e-6, v 4.5e-5, p 4.8e-4 with R-theta (the floor margin and the shear
 layers' rounding), rho 1.8e-6, v 1.1e-6, p 5.2e-6 with theta = 0 (no floor
-binds); t within 9.1e-7 (a_n from the FP32 lambda, rounded up by 2^-20).
+binds); t within 9.0e-7 (a_n from the FP32 lambda, rounded up by 2^-20).
 """
 
 import numpy as np
