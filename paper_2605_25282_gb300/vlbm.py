@@ -8,10 +8,16 @@ missing.
 Names follow the C ABI in include/vlbm.h: ``Ensemble`` wraps a ``vlbm_ctx``
 (vlbm_create / vlbm_init_ensemble / vlbm_step / vlbm_advance_to / vlbm_moments
 ...), and ``stats_w1_mean_std`` wraps the statistics call.
+
+Streams: every call is ordered after the work the caller has queued on its
+current stream, and the caller's current stream after the call, whichever
+stream the call itself runs on (an Ensemble's own, or a statistics call's
+``stream`` argument).
 """
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 from dataclasses import dataclass
@@ -398,6 +404,22 @@ def kernel_launches() -> int:
     return int(load_library().vlbm_kernel_launches())
 
 
+@contextlib.contextmanager
+def _on_stream(stream: torch.cuda.Stream | None, device):
+    """The stream a statistics call runs on (`stream`, else the caller's
+    current one), ordered after the work the caller has queued on its current
+    stream; on exit the caller's current stream is ordered after the call, so
+    its inputs and outputs are used in order wherever the caller goes on."""
+    cur = torch.cuda.current_stream(device)
+    s = stream if stream is not None else cur
+    other = s.cuda_stream != cur.cuda_stream
+    if other:
+        s.wait_stream(cur)
+    yield s
+    if other:
+        cur.wait_stream(s)
+
+
 def stats_w1_mean_std(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cuda.Stream | None = None):
     """Per-cell mean/std of both ensembles and one-point W1 (b restricted onto a's grid)."""
     _require_cuda()
@@ -410,10 +432,10 @@ def stats_w1_mean_std(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: torch.cu
     _, nyb, nxb = ens_b.shape
     dev = ens_a.device
     out = [torch.empty((nya, nxa), dtype=torch.float64, device=dev) for _ in range(5)]
-    s = stream if stream is not None else torch.cuda.current_stream(dev)
-    _check(lib.stats_w1_mean_std(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
-                                 int(ens_b.dtype == torch.float32), nxb, nyb, M, *[_ptr(o) for o in out],
-                                 ctypes.c_void_p(s.cuda_stream)))
+    with _on_stream(stream, dev) as s:
+        _check(lib.stats_w1_mean_std(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
+                                     int(ens_b.dtype == torch.float32), nxb, nyb, M, *[_ptr(o) for o in out],
+                                     ctypes.c_void_p(s.cuda_stream)))
     return dict(zip(("mean_a", "std_a", "mean_b", "std_b", "w1"), out))
 
 
@@ -426,9 +448,9 @@ def stats_restrict(ens: torch.Tensor, r: int, f32: bool = False, stream: torch.c
     ens = ens.contiguous()
     M, ny, nx = ens.shape
     out = torch.empty((M, ny // r, nx // r), dtype=torch.float32 if f32 else torch.float64, device=ens.device)
-    s = stream if stream is not None else torch.cuda.current_stream(ens.device)
-    _check(lib.stats_restrict(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, r, _ptr(out), int(f32),
-                              ctypes.c_void_p(s.cuda_stream)))
+    with _on_stream(stream, ens.device) as s:
+        _check(lib.stats_restrict(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, r, _ptr(out), int(f32),
+                                  ctypes.c_void_p(s.cuda_stream)))
     return out
 
 
@@ -444,10 +466,10 @@ def stats_w1_two_point(ens_a: torch.Tensor, ens_b: torch.Tensor, npd: int = 10,
     _, nyb, nxb = ens_b.shape
     w = torch.empty((), dtype=torch.float64, device=ens_a.device)
     pairs = torch.empty(npd ** 4, dtype=torch.float64, device=ens_a.device)
-    s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
-    _check(lib.stats_w1_two_point(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
-                                  int(ens_b.dtype == torch.float32), nxb, nyb, M, npd, _ptr(w), _ptr(pairs),
-                                  ctypes.c_void_p(s.cuda_stream)))
+    with _on_stream(stream, ens_a.device) as s:
+        _check(lib.stats_w1_two_point(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
+                                      int(ens_b.dtype == torch.float32), nxb, nyb, M, npd, _ptr(w), _ptr(pairs),
+                                      ctypes.c_void_p(s.cuda_stream)))
     return w, pairs
 
 
@@ -459,10 +481,10 @@ def stats_error_functionals(ens_a: torch.Tensor, ens_b: torch.Tensor, stream: to
     M, nya, nxa = ens_a.shape
     _, nyb, nxb = ens_b.shape
     out = torch.empty(4, dtype=torch.float64, device=ens_a.device)
-    s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
-    _check(lib.stats_error_functionals(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
-                                       int(ens_b.dtype == torch.float32), nxb, nyb, M, _ptr(out),
-                                       ctypes.c_void_p(s.cuda_stream)))
+    with _on_stream(stream, ens_a.device) as s:
+        _check(lib.stats_error_functionals(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya, _ptr(ens_b),
+                                           int(ens_b.dtype == torch.float32), nxb, nyb, M, _ptr(out),
+                                           ctypes.c_void_p(s.cuda_stream)))
     return out
 
 
@@ -484,10 +506,10 @@ def stats_error_functionals_noalloc(ens_a: torch.Tensor, ens_b: torch.Tensor, ou
     _, nyb, nxb = ens_b.shape
     # the scratch array is resolved for the current device: make it the tensors' one
     with torch.cuda.device(ens_a.device):
-        s = stream if stream is not None else torch.cuda.current_stream(ens_a.device)
-        _check(lib.stats_error_functionals_noalloc(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya,
-                                                   _ptr(ens_b), int(ens_b.dtype == torch.float32), nxb, nyb, M,
-                                                   _ptr(out), ctypes.c_void_p(s.cuda_stream)))
+        with _on_stream(stream, ens_a.device) as s:
+            _check(lib.stats_error_functionals_noalloc(_ptr(ens_a), int(ens_a.dtype == torch.float32), nxa, nya,
+                                                       _ptr(ens_b), int(ens_b.dtype == torch.float32), nxb, nyb, M,
+                                                       _ptr(out), ctypes.c_void_p(s.cuda_stream)))
     return out
 
 
@@ -499,9 +521,10 @@ def stats_quantiles(ens: torch.Tensor, probs, stream: torch.cuda.Stream | None =
     M, ny, nx = ens.shape
     pr = np.ascontiguousarray(probs, dtype=np.float64)
     out = torch.empty((len(pr), ny, nx), dtype=torch.float64, device=ens.device)
-    s = stream if stream is not None else torch.cuda.current_stream(ens.device)
-    _check(lib.stats_quantiles(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M,
-                               pr.ctypes.data_as(ctypes.c_void_p), len(pr), _ptr(out), ctypes.c_void_p(s.cuda_stream)))
+    with _on_stream(stream, ens.device) as s:
+        _check(lib.stats_quantiles(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M,
+                                   pr.ctypes.data_as(ctypes.c_void_p), len(pr), _ptr(out),
+                                   ctypes.c_void_p(s.cuda_stream)))
     return out
 
 
@@ -513,9 +536,9 @@ def stats_histogram(ens: torch.Tensor, edges: torch.Tensor, stream: torch.cuda.S
     M, ny, nx = ens.shape
     e = edges.to(ens.device, torch.float64).contiguous()
     out = torch.empty((e.numel() - 1, ny, nx), dtype=torch.float64, device=ens.device)
-    s = stream if stream is not None else torch.cuda.current_stream(ens.device)
-    _check(lib.stats_histogram(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, _ptr(e), e.numel() - 1,
-                               _ptr(out), ctypes.c_void_p(s.cuda_stream)))
+    with _on_stream(stream, ens.device) as s:
+        _check(lib.stats_histogram(_ptr(ens), int(ens.dtype == torch.float32), nx, ny, M, _ptr(e), e.numel() - 1,
+                                   _ptr(out), ctypes.c_void_p(s.cuda_stream)))
     return out
 
 

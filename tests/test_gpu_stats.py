@@ -125,3 +125,24 @@ def test_two_point_w1_identities():
     # a translated copy: every joint law moves by (0.1, 0.1)
     w, pairs = vlbm.stats_w1_two_point(a, a + 0.1, 4)
     assert torch.allclose(pairs, torch.full_like(pairs, 0.1 * np.sqrt(2.0)), rtol=1e-12)
+
+
+def test_statistics_on_another_stream_are_ordered_with_the_callers():
+    # inputs written on the caller's stream just before the call and results
+    # copied there just after, while the call runs on another stream: the
+    # binding orders both ways, so the copies equal a call on the caller's
+    # own stream after a synchronization
+    M, ny, nx = 256, 200, 300
+    side = torch.cuda.Stream()
+    g = torch.Generator(device="cuda").manual_seed(3)
+    base = torch.rand((M, ny, nx), device="cuda", dtype=torch.float64, generator=g) + 0.5
+    torch.cuda.synchronize()
+    for _ in range(3):
+        a = torch.exp(torch.log(base))  # queued on the caller's stream
+        b = torch.exp(torch.log(base.flip(0) * 1.1))
+        got = {k: v.clone() for k, v in vlbm.stats_w1_mean_std(a, b, stream=side).items()}
+        torch.cuda.synchronize()
+        ref = vlbm.stats_w1_mean_std(a, b)
+        torch.cuda.synchronize()
+        for k in ("mean_a", "std_a", "mean_b", "std_b", "w1"):
+            assert torch.equal(got[k], ref[k]), k
